@@ -1,0 +1,436 @@
+"""Throughput of the hyper-ROM FE^2 online step on GB300.
+
+A step is one monolithic Newton iteration of the hot path over a fixed
+synthetic batch: macro deformation gradient at every macro Gauss point ->
+batched hyper-reduced RVE evaluation (polar split, micro update, ECM loop,
+static condensation, rotation back) -> macro element assembly of R and K ->
+convergence scalars.  The metric is RVE evaluations per second (one
+evaluation = one macro point in one Newton iteration).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2]
+                  [--precision mixed|fp64] [--impl ours|reference]
+
+Default workload c2: 2D plane strain, 48x48 Q4 RVE with 4 inclusions, 24
+modes, 200 ECM points, plate with a central hole (O-grid 4 x 32 x 32 Q4,
+16384 macro Gauss points).  The CPU baseline and the reference arm time the
+float64 oracle as it stands on a bounded sample of the same points.
+"""
+import os
+
+for _v in ('OMP_NUM_THREADS', 'OPENBLAS_NUM_THREADS', 'MKL_NUM_THREADS'):
+    os.environ.setdefault(_v, '1')
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+from synthetic import meshes  # noqa: E402
+
+METRIC = "hyper-ROM RVE evals/s on 1 GB300, batched FP32/FP64 vs plain FP64, P̄ err ≤1e-8"
+UNIT = "RVE evals/s"
+
+WORKLOADS = {
+    'c1': dict(roms=['c1'], d=2, mesh=('rect', (4, 4)), load=0.10, desc='2D 16x16 Q4 RVE, 12 modes, 60 ECM points, 4x4 Q4 macro (64 points)'),
+    'c2': dict(roms=['c2'], d=2, mesh=('plate', (32, 32)), load=0.15,
+               desc='2D 48x48 Q4 RVE (4 inclusions), 24 modes, 200 ECM points, plate with hole 4x32x32 Q4 (16384 points)'),
+    'c3': dict(roms=['c3'], d=3, mesh=('box', (32, 32, 8, 4.0, 4.0, 1.0)), load=0.20,
+               desc='3D 16^3 hex8 RVE, 40 modes, 400 ECM points, 32x32x8 hex8 cantilever (65536 points)'),
+    'c4': dict(roms=['c1'], d=2, mesh=('rect', (64, 64)), load=0.10,
+               desc='2D 16x16 Q4 RVE, 12 modes, 60 ECM points, 64x64 Q4 macro (16384 points)'),
+    'c5': dict(roms=['c5a', 'c5b', 'c5c'], d=2, mesh=('rect', (181, 181)), load=0.14,
+               desc='2D mixed batch of 3 RVE types (16/32/64 modes, 120/300/600 ECM points), 181x181 Q4 (131044 points)'),
+}
+
+# algorithmic work per evaluation (FP64 FLOP of kinematics + residual + law,
+# symmetric-half tangent contraction FLOP), per ROM type
+def work_per_eval(rom):
+    m, g, n = rom['B'].shape
+    d = int(round(np.sqrt(g)))
+    law = 150 if d == 2 else 400
+    fp64 = 2 * m * g * n * 2 + m * (law + 2 * g)
+    fp32 = n * (n + 1) * m * g + 2 * m * g * g * n
+    return fp64, fp32
+
+
+def macro_displacement(X, load, seed):
+    """Smooth synthetic macro displacement: uniform stretch `load/2` plus
+    seeded sine modes with displacement gradients of about load/3."""
+    g = syn.rng(seed)
+    d = X.shape[1]
+    L = X.max(0) - X.min(0)
+    u = 0.5 * load * X.copy()
+    for k in range(1, 4):
+        for i in range(d):
+            ph = g.random(d) * 2 * np.pi
+            amp = (load / 3.0) * (g.random() - 0.5) / (k * np.pi) * L.min()
+            arg = sum(2 * np.pi * k * X[:, j] / L[j] + ph[j] for j in range(d))
+            u[:, i] += amp * np.sin(arg)
+    return u
+
+
+def build_mesh(spec):
+    kind, a = spec
+    if kind == 'rect':
+        return meshes.rect(*a)
+    if kind == 'box':
+        return meshes.box(*a)
+    return meshes.plate_with_hole(*a)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix='.csv')
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ['nvidia-smi', '-i', str(self.index),
+                 '--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,'
+                 'clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,'
+                 'clocks_event_reasons.sw_power_cap', '--format=csv,noheader,nounits', '-lms', '200'],
+                stdout=open(self.path, 'w'), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(',')]
+                if len(f) < 6:
+                    continue
+                try:
+                    sm.append(float(f[0]))
+                    mx.append(float(f[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[2:6]):
+                    if v.lower().startswith('active'):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(rom_paths, types, F, q, s, S, U, budget_s, max_points=None):
+    """Evaluations/s of the float64 oracle (single thread) on a bounded sample."""
+    from oracle import reduced
+    roms = [reduced.Rom.load(p) for p in rom_paths]
+    n = len(F)
+    cnt = 0
+    t0 = time.perf_counter()
+    a = 0
+    while True:
+        r = roms[types[a]]
+        k = r.n
+        reduced.eval_point(r, F[a], q[a][:k], s[a][:k], S[a][:k], U[a])
+        cnt += 1
+        a = (a + 1) % n
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_points and cnt >= max_points):
+            return cnt / el, cnt, el
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--workload', default='c2', choices=sorted(WORKLOADS))
+    ap.add_argument('--precision', default='mixed', choices=['mixed', 'fp64'])
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get('RANK', '0'))
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    rom_paths = [os.path.join(ROOT, 'tests', 'golden', 'rom_%s.npz' % r) for r in wl['roms']]
+
+    X, conn = build_mesh(wl['mesh'])
+    d = wl['d']
+    u_host = macro_displacement(X, wl['load'], syn.SEED_BASE + 500 + rank)
+
+    if args.impl == 'reference':
+        if rank != 0:
+            return 0
+        run_reference(args, wl, rom_paths, X, conn, u_host)
+        return 0
+
+    import torch
+    import paper_2306_02687_gb300 as rv
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl')
+    dev = torch.device('cuda', local)
+
+    roms = [rv.load_rom_file(p) for p in rom_paths]
+    h = rv.rve_rom_create(d, roms, roms[0]['V0'])
+    mesh = rv.macro_mesh_create(X, conn)
+    n = mesh.n_ip
+    types = None
+    types_np = np.zeros(n, dtype=np.int32)
+    if len(roms) > 1:
+        types_np = syn.type_labels(syn.SEED_BASE + 600 + rank, n, len(roms))
+        types = torch.tensor(types_np, device=dev)
+    u = torch.tensor(u_host, device=dev)
+    Fbar = torch.empty(n, d * d, dtype=torch.float64, device=dev)
+    rv.macro_gradient(mesh, u, Fbar)
+    q, s, S, U = h.zero_state(n)
+    Pbar, dPdF, rnorm, status = h.outputs(n)
+    R = torch.empty(mesh.n_dof, dtype=torch.float64, device=dev)
+    Kv = torch.empty(mesh.nnz, dtype=torch.float64, device=dev)
+    free = torch.ones(mesh.n_dof, dtype=torch.uint8, device=dev)
+    norms = torch.empty(3, dtype=torch.float64, device=dev)
+
+    # mid-Newton state: micro states converged at Fbar (float64 staggered
+    # iterations), then q perturbed by 1e-3 of its size
+    for _ in range(8):
+        rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision='fp64')
+    g = torch.Generator(device='cpu').manual_seed(syn.SEED_BASE + 700 + rank)
+    pert = torch.randn(q.shape, generator=g, dtype=torch.float64).to(dev)
+    q += 1e-3 * q.abs().amax(dim=1, keepdim=True) * pert * (q != 0)
+    s.zero_()
+    S.zero_()
+    torch.cuda.synchronize()
+    bad = int((status != 0).sum().item())
+    state0 = [x.clone() for x in (q, s, S, U)]
+
+    def restore():
+        for x, y in zip((q, s, S, U), state0):
+            x.copy_(y)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(precision, ev=None):
+        rv.macro_gradient(mesh, u, Fbar)
+        if ev is not None:
+            ev[0].record(stream)
+        rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=precision)
+        if ev is not None:
+            ev[1].record(stream)
+        rv.macro_assemble(mesh, Pbar, dPdF, R, Kv)
+        rv.macro_residual_norms(mesh, R, free, rnorm, norms)
+
+    def timed(precision, steps, warmup):
+        restore()
+        for _ in range(warmup):
+            step(precision)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        tot, kern = 0.0, 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            step(precision, (e[1], e[2]))
+            e[3].record(stream)
+            e[3].synchronize()
+            tot += e[0].elapsed_time(e[3])
+            kern += e[1].elapsed_time(e[2])
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return tot / steps, kern / steps
+
+    with ClockSampler(local) as clk:
+        ms_step, ms_kern = timed(args.precision, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_max = ms_step
+    if dist:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = t.item()
+    value = world * n / (ms_max * 1e-3)
+
+    # plain float64 GPU form on the same workload (speedup denominator)
+    other = 'fp64' if args.precision == 'mixed' else 'mixed'
+    ms_other, _ = timed(other, max(2, min(args.steps, 5)), 1)
+
+    # accuracy of the timed form against the float64 form on every point
+    restore()
+    rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=args.precision)
+    P1, C1 = Pbar.clone(), dPdF.clone()
+    restore()
+    rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision='fp64')
+    torch.cuda.synchronize()
+    pn = Pbar.abs().amax(dim=1).clamp_min(1e-300)
+    cn = dPdF.abs().amax(dim=(1, 2)).clamp_min(1e-300)
+    p_err = ((P1 - Pbar).abs().amax(dim=1) / pn).max().item()
+    c_err = ((C1 - dPdF).abs().amax(dim=(1, 2)) / cn).max().item()
+
+    # end to end through the public API: pinned host u in, R / K / norms out
+    u_pin = torch.tensor(u_host).pin_memory()
+    R_pin = torch.empty(mesh.n_dof, dtype=torch.float64).pin_memory()
+    K_pin = torch.empty(mesh.nnz, dtype=torch.float64).pin_memory()
+    nrm_pin = torch.empty(3, dtype=torch.float64).pin_memory()
+    restore()
+    e2e_steps = max(2, min(args.steps, 10))
+    for it in range(1 + e2e_steps):
+        if it == 1:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        u.copy_(u_pin, non_blocking=True)
+        step(args.precision)
+        R_pin.copy_(R, non_blocking=True)
+        K_pin.copy_(Kv, non_blocking=True)
+        nrm_pin.copy_(norms, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / e2e_steps
+    if dist:
+        t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = t.item()
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (the batched RVE evaluation)
+    n_per_type = np.bincount(types_np, minlength=len(roms))
+    w64 = sum(c * work_per_eval(r)[0] for c, r in zip(n_per_type, roms))
+    w32 = sum(c * work_per_eval(r)[1] for c, r in zip(n_per_type, roms))
+    if args.precision == 'fp64':
+        achieved = (w64 + w32) / (ms_kern * 1e-3) / 1e12
+        peak = 1.25
+        bound_unit = 'fp64 pipe'
+    else:
+        achieved = w64 / (ms_kern * 1e-3) / 1e12
+        peak = 1.25
+        bound_unit = 'fp64 pipe (FP64-accurate F_i, P_i, r, Pbar)'
+    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "rverom::eval_kernel", "binding": bound_unit,
+                "peak_source": "nominal FP64 rate 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "kernel_ms": ms_kern, "fp32_tflops_achieved": w32 / (ms_kern * 1e-3) / 1e12}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        Fh = Fbar.cpu().numpy().reshape(n, d, d)
+        sel = np.arange(0, n, max(1, n // 512))[:512]
+        restore()
+        st = [x.cpu().numpy() for x in (q, s, S, U)]
+        rate, cnt, el = oracle_rate(rom_paths, types_np[sel], Fh[sel], st[0][sel], st[1][sel], st[2][sel],
+                                    st[3][sel], budget_s=12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d evaluations (cycling over %d of the %d points) in %.1f s, float64 NumPy oracle, one thread"
+                         % (cnt, len(sel), n, el)}
+
+    launches = 4 * args.steps  # gradient, evaluation, assembly, norms (single type)
+    if len(roms) > 1:
+        launches = (3 + 3 + len(roms)) * args.steps
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32" if args.precision == 'mixed' else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ': ' + wl['desc'], "macro_points_per_gpu": n,
+                   "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                   "state": "mid-Newton (converged micro state, q perturbed by 1e-3 |q|)",
+                   "failed_points": bad},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(u_pin.numel() * 8),
+                "d2h_bytes_per_step": int((R_pin.numel() + K_pin.numel() + 3) * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "other_form": {"precision": other, "value": world * n / (ms_other * 1e-3), "ms_per_step": ms_other},
+        "speedup_vs_fp64_form": (ms_other / ms_step) if args.precision == 'mixed' else 1.0,
+        "accuracy_vs_fp64_form": {"Pbar_rel_err_max": p_err, "dPdF_rel_err_max": c_err},
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference(args, wl, rom_paths, X, conn, u_host):
+    """The oracle as it stands on the host cores, same metric and workload:
+    each step is a bounded sample of the workload's macro points."""
+    from oracle import macro as omacro, reduced
+    d = wl['d']
+    mesh = omacro.MacroMesh(X, conn)
+    Fh = mesh.gradient(u_host)
+    n = mesh.n_ip
+    types = np.zeros(n, dtype=np.int64)
+    if len(rom_paths) > 1:
+        types = syn.type_labels(syn.SEED_BASE + 600, n, len(rom_paths)).astype(np.int64)
+    roms = [reduced.Rom.load(p) for p in rom_paths]
+    per_step = 1024
+    sel = np.arange(0, n, max(1, n // per_step))[:per_step]
+    states = []
+    for a in sel:
+        r = roms[types[a]]
+        st = reduced.zero_state(r)
+        from oracle import polar, rve
+        st['Uprev'] = rve.to_voigt(polar.polar(Fh[a])[1])
+        states.append(st)
+
+    def one_step():
+        for k, a in enumerate(sel):
+            r = roms[types[a]]
+            o = reduced.eval_point(r, Fh[a], **states[k])
+        return o
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    el = time.perf_counter() - t0
+    rate = len(sel) * args.steps / el
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": args.workload + ': ' + wl['desc'], "sample_points_per_step": len(sel)},
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "%d of the %d macro points per step, float64 NumPy oracle, one thread"
+                                      % (len(sel), n)},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == '__main__':
+    sys.exit(main())

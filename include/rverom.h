@@ -1,0 +1,174 @@
+/*
+ * rverom.h -- C ABI of the GB300 (sm_103a) hyper-reduced FE^2 online path.
+ *
+ * Method: Lange, Huetter, Kiefer, "A Monolithic Hyper ROM FE^2 Method with
+ * Clustered Training at Finite Deformations", arXiv 2306.02687.
+ *
+ * Conventions shared by every entry point
+ *   d      spatial dimension, 2 (plane strain) or 3
+ *   g      d*d components of a second-order tensor, row-major: c = i*d + J
+ *   ns     3 (2D) or 6 (3D) independent components of a symmetric tensor,
+ *          order 2D (11,22,12), 3D (11,22,33,12,13,23), tensor (not
+ *          engineering) components
+ *   n~     ROM modes of an RVE type, m~ its ECM (hyper-integration) points
+ *   nmax   largest n~ over the types of a handle; per-point state arrays are
+ *          padded to nmax
+ * Pointers named "device" must be CUDA device pointers on the current device;
+ * "host" pointers are ordinary host memory.  The library never takes
+ * ownership of caller memory.  All device work is enqueued on `stream`
+ * (a cudaStream_t passed as void*, NULL = legacy default stream) and is
+ * asynchronous with respect to the host unless stated otherwise.
+ *
+ * Return values: RVEROM_OK (0) or a negative RVEROM_ERR_* code.  Argument
+ * errors are detected on the host before anything is enqueued.  Numerical
+ * failures of single macro points are not API errors: they are reported per
+ * point in `status` (RVEROM_STATUS_*), never by trapping the GPU.
+ */
+#ifndef RVEROM_H
+#define RVEROM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RVEROM_OK 0
+#define RVEROM_ERR_ARG (-1)         /* bad size, null pointer, unsupported shape */
+#define RVEROM_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define RVEROM_ERR_UNSUPPORTED (-3) /* n~ or d outside the compiled kernels */
+
+#define RVEROM_STATUS_OK 0
+#define RVEROM_STATUS_DETF_NONPOS 1 /* det F <= 0 at some ECM point */
+#define RVEROM_STATUS_NONSPD_K 2    /* reduced stiffness not positive definite */
+#define RVEROM_STATUS_NONFINITE 3   /* NaN/Inf in the input or the reduced system */
+
+#define RVEROM_FP64 0  /* every step in native float64 */
+#define RVEROM_MIXED 1 /* FP64-accurate F_i, P_i, r, Pbar; float32 tangent contraction */
+
+#define RVEROM_MAX_TYPES 8
+
+typedef struct rverom_s *rverom_t;
+typedef struct rverom_mesh_s *rverom_mesh_t;
+
+/* One RVE type of the hyper-ROM (all arrays host, copied by rve_rom_create).
+ *   B      [n_ecm][g][n_modes] gradient of the POD modes at the ECM points,
+ *          B_i = grad Phi (x_i): F_i = U + B_i q  (ROM ansatz, Sec. 3.2.1,
+ *          Eq. ROM_assumption; element-mode projection of Sec. 4)
+ *   w      [n_ecm] ECM weights in the reference volume (Sec. 3.3, Box 1),
+ *          positive, summing to V0
+ *   phase  [n_ecm] material phase of each ECM point, 0 or 1
+ *   moduli [2][2] (mu, kappa) of phase 0 and phase 1 of the compressible
+ *          Neo-Hooke law P = mu (F - F^-T) + (kappa - 2 mu/3) ln J F^-T      */
+typedef struct {
+    int32_t n_modes;
+    int32_t n_ecm;
+    const double *B;
+    const double *w;
+    const int32_t *phase;
+    double moduli[2][2];
+} rverom_type_desc;
+
+/* Create a handle holding device copies of the ROM tables of n_types RVE
+ * types (1..RVEROM_MAX_TYPES) of dimension dim, reference volume V0.
+ * Supported n_modes: 2D 1..64, 3D 1..47.  Synchronous; allocates device
+ * memory (tables and a small reduction workspace).  On error *out is NULL. */
+int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_desc *types, double V0,
+                   rverom_t *out);
+
+/* Free the handle and its device memory (synchronizes the device). */
+int rve_rom_destroy(rverom_t h);
+
+/* Replace the moduli of one type (host [2][2] = (mu, kappa) per phase).
+ * Takes effect for work enqueued after the call returns. */
+int rve_rom_set_moduli(rverom_t h, int32_t type, const double *moduli);
+
+/* Largest n~ of the handle (the padding of the per-point state arrays). */
+int rve_rom_nmax(rverom_t h, int32_t *nmax);
+
+/* Batched hyper-reduced RVE evaluation at n_points macro integration points:
+ * one monolithic Newton evaluation per point (Sec. 3.2.2-3.2.3, Sec. 4):
+ *   a1  Fbar = R U (polar split, Eq. polar_decomp); micro update
+ *       q <- q - s - S (U - U_prev)                 (Sec. 3.2.3, Delta u~)
+ *   a2  F_i = U + B_i q at every ECM point          (Eq. ROM_assumption)
+ *   a3  P_i, A_i = dP/dF from the micro law
+ *   a4  r = sum w_i B_i^T P_i, Pbar_U = sum w_i P_i / V0  (Eq. ROMintforce, Eq. 2)
+ *   a5  K = sum w_i B_i^T A_i B_i, K_qF = sum w_i B_i^T A_i, K_FF = sum w_i A_i
+ *                                                     (Eq. ROMstiffness)
+ *   a6  s = K^-1 r, S = K^-1 K_qF E, Pbar_alg = Pbar_U - K_qF^T s / V0,
+ *       C_U = (K_FF - K_qF^T K^-1 K_qF) / V0          (Eq. Biot_Tangent, condensation)
+ *   a7  Pbar = R Pbar_alg, dPdF = dPbar/dFbar through the polar derivative
+ * Arguments (all device, row-major, contiguous):
+ *   type    [n] int32 RVE type per point, or NULL when every point is type 0
+ *   Fbar    [n][g]            macro deformation gradient (in)
+ *   q, s    [n][nmax]         reduced amplitudes and K^-1 r (in/out state)
+ *   S       [n][nmax][ns]     K^-1 dr/dU (in/out state)
+ *   Uprev   [n][ns]           stretch of the previous evaluation (in/out)
+ *   Pbar    [n][g]            homogenized 1st Piola-Kirchhoff stress (out)
+ *   dPdF    [n][g][g]         consistent tangent dPbar_c/dFbar_e at [c][e] (out)
+ *   rnorm   [n]               max_j |r_j| of the evaluated state (out)
+ *   status  [n]               RVEROM_STATUS_* (out)
+ * A fresh state is q = s = S = 0 and Uprev = the Voigt stretch of Fbar (or
+ * of I).  Points whose status is not OK keep their input state; their Pbar
+ * and dPdF are NaN.  precision: RVEROM_FP64 or RVEROM_MIXED.  n_points may be
+ * 0 (no work).  Points with a type >= n_types get RVEROM_STATUS_NONFINITE. */
+int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *type, const double *Fbar,
+                       double *q, double *s, double *S, double *Uprev, double *Pbar, double *dPdF,
+                       double *rnorm, int32_t *status, int32_t precision, void *stream);
+
+/* Implicit-function adjoint at converged states (r(q*) = 0): for cotangents
+ * gPbar on Pbar,
+ *   gFbar = dPdF^T gPbar      (the condensed consistent tangent)
+ *   gTheta[t][ph][k] += sum over points of type t of d<gPbar, Pbar>/d theta,
+ *       theta = (mu, kappa) of phase ph, computed as
+ *       (1/V0) sum_i w_i < R^T gPbar - B_i z , dP_i/dtheta >,
+ *       z = K^-1 K_qF (R^T gPbar)
+ * Device arrays: type [n] or NULL, Fbar [n][g], q [n][nmax], gPbar [n][g],
+ * gFbar [n][g] (out), gTheta [n_types][2][2] (accumulated, deterministic
+ * order), status [n] (out, as in rve_rom_eval_batch).  Uses the handle's
+ * reduction workspace, so calls on one handle must not overlap. */
+int rve_rom_adjoint(rverom_t h, int64_t n_points, const int32_t *type, const double *Fbar,
+                    const double *q, const double *gPbar, double *gFbar, double *gTheta,
+                    int32_t *status, void *stream);
+
+/* Macro mesh of isoparametric Q4 (dim 2) or hex8 (dim 3) elements with 2^d
+ * Gauss points each; integration point alpha = e * 2^d + gp (gp in
+ * lexicographic order of the reference coordinates, last coordinate slowest
+ * ... first fastest).  X [n_nodes][d] and conn [n_elem][2^d] are host arrays.
+ * Builds, on the host, the shape-function gradients and weights of every
+ * point and the CSR pattern of the global stiffness (one row per DOF
+ * node*d + i), then copies them to the device.  Synchronous. */
+int macro_mesh_create(int32_t dim, int64_t n_nodes, int64_t n_elem, const double *X,
+                      const int64_t *conn, rverom_mesh_t *out);
+int macro_mesh_destroy(rverom_mesh_t m);
+
+/* Sizes of a mesh: integration points, DOFs, CSR non-zeros. */
+int macro_mesh_sizes(rverom_mesh_t m, int64_t *n_ip, int64_t *n_dof, int64_t *nnz);
+
+/* Copy the CSR pattern to host arrays row_ptr [n_dof+1], col [nnz]. */
+int macro_mesh_csr(rverom_mesh_t m, int64_t *row_ptr, int32_t *col);
+
+/* Fbar at every integration point from nodal displacements (device
+ * u [n_nodes][d] -> Fbar [n_ip][g]): Fbar = I + sum_a u_a (x) grad N_a. */
+int macro_gradient(rverom_mesh_t m, const double *u, double *Fbar, void *stream);
+
+/* Macro element assembly (Eq. 6 with Pbar; its linearization with dPdF):
+ *   R[a*d+i]  = sum_alpha wJ0 sum_J Pbar_iJ dN_a,J
+ *   K[(a,i),(b,k)] = sum_alpha wJ0 sum_JL dN_a,J dPdF[iJ][kL] dN_b,L
+ * Device: Pbar [n_ip][g], dPdF [n_ip][g][g] (NULL skips K), R [n_dof] and
+ * Kvals [nnz] (CSR order of macro_mesh_csr) are overwritten. */
+int macro_assemble(rverom_mesh_t m, const double *Pbar, const double *dPdF, double *R,
+                   double *Kvals, void *stream);
+
+/* Convergence scalars of a monolithic iteration (device):
+ *   out[0] = max |R| over DOFs with free_mask != 0
+ *   out[1] = max |R| over DOFs with free_mask == 0 (reactions)
+ *   out[2] = max over points of rnorm
+ * free_mask [n_dof] uint8, rnorm [n_points]. */
+int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_mask,
+                         int64_t n_points, const double *rnorm, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -17,6 +17,8 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from synthetic import meshes
+
 from . import reduced
 
 _G1 = 1.0 / np.sqrt(3.0)
@@ -86,60 +88,15 @@ class MacroMesh:
 
 
 def rect_mesh(nx, ny, Lx=1.0, Ly=1.0):
-    xs, ys = np.linspace(0, Lx, nx + 1), np.linspace(0, Ly, ny + 1)
-    X = np.array([[x, y] for y in ys for x in xs])
-    conn = []
-    for j in range(ny):
-        for i in range(nx):
-            n0 = j * (nx + 1) + i
-            conn.append([n0, n0 + 1, n0 + nx + 2, n0 + nx + 1])
-    return MacroMesh(X, conn)
+    return MacroMesh(*meshes.rect(nx, ny, Lx, Ly))
 
 
 def box_mesh(nx, ny, nz, Lx, Ly, Lz):
-    xs, ys, zs = np.linspace(0, Lx, nx + 1), np.linspace(0, Ly, ny + 1), np.linspace(0, Lz, nz + 1)
-    X = np.array([[x, y, z] for z in zs for y in ys for x in xs])
-    conn = []
-    sx, sy = nx + 1, (nx + 1) * (ny + 1)
-    for k in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                n0 = k * sy + j * sx + i
-                b = [n0, n0 + 1, n0 + sx + 1, n0 + sx]
-                conn.append(b + [v + sy for v in b])
-    return MacroMesh(X, conn)
+    return MacroMesh(*meshes.box(nx, ny, nz, Lx, Ly, Lz))
 
 
 def plate_with_hole_mesh(nr, nt, half=1.0, radius=0.2):
-    """O-grid of 4 blocks (one per side of the square [-half, half]^2), each
-    nr (radial) x nt (tangential) Q4 elements between the hole and the outer
-    edge; blocks share their diagonal node lines."""
-    nodes, index = [], {}
-
-    def node(key, xy):
-        if key not in index:
-            index[key] = len(nodes)
-            nodes.append(xy)
-        return index[key]
-
-    # tangential parameter runs around the hole: block b covers angles
-    # [-45 + 90 b, 45 + 90 b] degrees; node (i radial, t global tangential)
-    ntot = 4 * nt
-    ids = np.zeros((nr + 1, ntot), dtype=np.int64)
-    for t in range(ntot):
-        ang = -np.pi / 4 + 2 * np.pi * t / ntot
-        c, s = np.cos(ang), np.sin(ang)
-        inner = radius * np.array([c, s])
-        outer = np.array([c, s]) * half / max(abs(c), abs(s))
-        for i in range(nr + 1):
-            f = i / nr
-            ids[i, t] = node((i, t), (1 - f) * inner + f * outer)
-    conn = []
-    for t in range(ntot):
-        t1 = (t + 1) % ntot
-        for i in range(nr):
-            conn.append([ids[i, t], ids[i + 1, t], ids[i + 1, t1], ids[i, t1]])
-    return MacroMesh(np.array(nodes), conn)
+    return MacroMesh(*meshes.plate_with_hole(nr, nt, half, radius))
 
 
 class Problem:

@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) hyper-reduced FE^2 online path.
+
+Implements, from Lange, Huetter, Kiefer, "A Monolithic Hyper ROM FE^2 Method
+with Clustered Training at Finite Deformations" (arXiv 2306.02687), the
+batched evaluation of the ROM/ECM-reduced RVE at every macro integration
+point of a monolithic Newton iteration, its static condensation into the
+homogenized stress and consistent tangent, the macro element assembly and the
+implicit adjoint, as CUDA kernels behind the C ABI of include/rverom.h.
+
+Python entry points (thin marshalling over librverom.so, see api.py):
+  rve_rom_create, rve_rom_set_moduli, rve_rom_eval_batch, rve_rom_adjoint,
+  macro_mesh_create, macro_gradient, macro_assemble, macro_residual_norms
+"""
+from .api import (FP64, MIXED, RomHandle, MeshHandle, load_rom_file, rve_rom_create,  # noqa: F401
+                  rve_rom_set_moduli, rve_rom_eval_batch, rve_rom_adjoint, macro_mesh_create,
+                  macro_gradient, macro_assemble, macro_residual_norms)

@@ -1,0 +1,221 @@
+"""Thin Python binding of librverom (include/rverom.h).
+
+Argument marshalling only: every step of the hyper-ROM path runs in the CUDA
+kernels of the native library.  Tensors are torch CUDA tensors (device memory
+and streams come from PyTorch); each function checks dtype, device, shape and
+contiguity, passes raw pointers and the current CUDA stream, and raises on a
+non-zero return code.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+
+FP64 = 0
+MIXED = 1
+_PREC = {'fp64': FP64, 'mixed': MIXED, FP64: FP64, MIXED: MIXED}
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype, shape=None, name='tensor'):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError('%s must be a CUDA tensor' % name)
+    if t.dtype != dtype:
+        raise TypeError('%s must be %s, got %s' % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError('%s must be contiguous' % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError('%s must have shape %s, got %s' % (name, tuple(shape), tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def load_rom_file(path):
+    """Host arrays of a ROM file: dict(B, w, phase, moduli, V0)."""
+    z = np.load(path)
+    return dict(B=np.ascontiguousarray(z['B'], dtype=np.float64),
+                w=np.ascontiguousarray(z['w'], dtype=np.float64),
+                phase=np.ascontiguousarray(z['phase'], dtype=np.int32),
+                moduli=np.ascontiguousarray(z['moduli'], dtype=np.float64),
+                V0=float(z['V0']))
+
+
+class RomHandle:
+    """Owns an rverom_t (device copies of the ROM tables of n_types types)."""
+
+    def __init__(self, ptr, dim, n_types, nmax, V0):
+        self.ptr = ptr
+        self.dim = dim
+        self.g = dim * dim
+        self.ns = 3 if dim == 2 else 6
+        self.n_types = n_types
+        self.nmax = nmax
+        self.V0 = V0
+
+    def destroy(self):
+        if self.ptr:
+            _native.check(_native.lib().rve_rom_destroy(self.ptr), 'rve_rom_destroy')
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def zero_state(self, n, Fbar=None):
+        """Fresh per-point state tensors (q, s, S, Uprev) on the current device;
+        Uprev holds the Voigt stretch of I (or of the polar stretch of Fbar
+        when given, computed on the host only for initialization)."""
+        dev = torch.device('cuda')
+        q = torch.zeros(n, self.nmax, dtype=torch.float64, device=dev)
+        s = torch.zeros_like(q)
+        S = torch.zeros(n, self.nmax, self.ns, dtype=torch.float64, device=dev)
+        U = torch.zeros(n, self.ns, dtype=torch.float64, device=dev)
+        U[:, :self.dim] = 1.0
+        return q, s, S, U
+
+    def outputs(self, n):
+        dev = torch.device('cuda')
+        return (torch.empty(n, self.g, dtype=torch.float64, device=dev),
+                torch.empty(n, self.g, self.g, dtype=torch.float64, device=dev),
+                torch.empty(n, dtype=torch.float64, device=dev),
+                torch.empty(n, dtype=torch.int32, device=dev))
+
+
+def rve_rom_create(dim, types, V0=1.0):
+    """types: list of dicts with B [m][g][n], w [m], phase [m], moduli [2][2]."""
+    n_types = len(types)
+    descs = (_native.TypeDesc * n_types)()
+    keep = []
+    for t, ty in enumerate(types):
+        B = np.ascontiguousarray(ty['B'], dtype=np.float64)
+        w = np.ascontiguousarray(ty['w'], dtype=np.float64)
+        ph = np.ascontiguousarray(ty['phase'], dtype=np.int32)
+        mod = np.asarray(ty['moduli'], dtype=np.float64)
+        if B.ndim != 3 or B.shape[1] != dim * dim or B.shape[0] != w.shape[0] or ph.shape != w.shape:
+            raise ValueError('bad ROM table shapes for type %d' % t)
+        keep += [B, w, ph]
+        d = descs[t]
+        d.n_modes = B.shape[2]
+        d.n_ecm = B.shape[0]
+        d.B = B.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.phase = ph.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        for a in range(2):
+            for b in range(2):
+                d.moduli[a][b] = float(mod[a, b])
+    out = ctypes.c_void_p()
+    L = _native.lib()
+    torch.cuda.current_device()  # make sure the CUDA context exists on the current device
+    _native.check(L.rve_rom_create(dim, n_types, descs, float(V0), ctypes.byref(out)), 'rve_rom_create')
+    nmax = ctypes.c_int32()
+    _native.check(L.rve_rom_nmax(out, ctypes.byref(nmax)), 'rve_rom_nmax')
+    return RomHandle(out, dim, n_types, nmax.value, float(V0))
+
+
+def rve_rom_set_moduli(h, type_id, moduli):
+    m = np.ascontiguousarray(moduli, dtype=np.float64).reshape(4)
+    _native.check(_native.lib().rve_rom_set_moduli(h.ptr, int(type_id),
+                                                   m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                  'rve_rom_set_moduli')
+
+
+def rve_rom_eval_batch(h, Fbar, q, s, S, Uprev, Pbar, dPdF, rnorm, status, type=None,
+                       precision='mixed', stream=None):
+    n = Fbar.shape[0]
+    g, ns, nm = h.g, h.ns, h.nmax
+    args = [_ptr(type, torch.int32, (n,), 'type') if type is not None else None,
+            _ptr(Fbar, torch.float64, (n, g), 'Fbar'),
+            _ptr(q, torch.float64, (n, nm), 'q'), _ptr(s, torch.float64, (n, nm), 's'),
+            _ptr(S, torch.float64, (n, nm, ns), 'S'), _ptr(Uprev, torch.float64, (n, ns), 'Uprev'),
+            _ptr(Pbar, torch.float64, (n, g), 'Pbar'), _ptr(dPdF, torch.float64, (n, g, g), 'dPdF'),
+            _ptr(rnorm, torch.float64, (n,), 'rnorm'), _ptr(status, torch.int32, (n,), 'status')]
+    rc = _native.lib().rve_rom_eval_batch(h.ptr, n, *args, _PREC[precision], _stream(stream))
+    _native.check(rc, 'rve_rom_eval_batch')
+
+
+def rve_rom_adjoint(h, Fbar, q, gPbar, gFbar, gTheta, status, type=None, stream=None):
+    n = Fbar.shape[0]
+    g, nm = h.g, h.nmax
+    args = [_ptr(type, torch.int32, (n,), 'type') if type is not None else None,
+            _ptr(Fbar, torch.float64, (n, g), 'Fbar'), _ptr(q, torch.float64, (n, nm), 'q'),
+            _ptr(gPbar, torch.float64, (n, g), 'gPbar'), _ptr(gFbar, torch.float64, (n, g), 'gFbar'),
+            _ptr(gTheta, torch.float64, (h.n_types, 2, 2), 'gTheta'),
+            _ptr(status, torch.int32, (n,), 'status')]
+    _native.check(_native.lib().rve_rom_adjoint(h.ptr, n, *args, _stream(stream)), 'rve_rom_adjoint')
+
+
+class MeshHandle:
+    def __init__(self, ptr, dim, n_nodes, n_elem):
+        self.ptr = ptr
+        self.dim = dim
+        self.g = dim * dim
+        self.n_nodes = n_nodes
+        self.n_elem = n_elem
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _native.check(_native.lib().macro_mesh_sizes(ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                      'macro_mesh_sizes')
+        self.n_ip, self.n_dof, self.nnz = a.value, b.value, c.value
+
+    def csr(self):
+        rp = np.zeros(self.n_dof + 1, dtype=np.int64)
+        col = np.zeros(self.nnz, dtype=np.int32)
+        _native.check(_native.lib().macro_mesh_csr(self.ptr, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                   col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+                      'macro_mesh_csr')
+        return rp, col
+
+    def destroy(self):
+        if self.ptr:
+            _native.check(_native.lib().macro_mesh_destroy(self.ptr), 'macro_mesh_destroy')
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def macro_mesh_create(X, conn):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    conn = np.ascontiguousarray(conn, dtype=np.int64)
+    dim = X.shape[1]
+    out = ctypes.c_void_p()
+    torch.cuda.current_device()
+    _native.check(_native.lib().macro_mesh_create(dim, X.shape[0], conn.shape[0],
+                                                  X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                  conn.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                  ctypes.byref(out)), 'macro_mesh_create')
+    return MeshHandle(out, dim, X.shape[0], conn.shape[0])
+
+
+def macro_gradient(m, u, Fbar, stream=None):
+    _native.check(_native.lib().macro_gradient(m.ptr, _ptr(u, torch.float64, (m.n_nodes, m.dim), 'u'),
+                                               _ptr(Fbar, torch.float64, (m.n_ip, m.g), 'Fbar'),
+                                               _stream(stream)), 'macro_gradient')
+
+
+def macro_assemble(m, Pbar, dPdF, R, Kvals=None, stream=None):
+    _native.check(_native.lib().macro_assemble(
+        m.ptr, _ptr(Pbar, torch.float64, (m.n_ip, m.g), 'Pbar'),
+        _ptr(dPdF, torch.float64, (m.n_ip, m.g, m.g), 'dPdF') if dPdF is not None else None,
+        _ptr(R, torch.float64, (m.n_dof,), 'R'),
+        _ptr(Kvals, torch.float64, (m.nnz,), 'Kvals') if Kvals is not None else None,
+        _stream(stream)), 'macro_assemble')
+
+
+def macro_residual_norms(m, R, free_mask, rnorm, out, stream=None):
+    n = rnorm.shape[0]
+    _native.check(_native.lib().macro_residual_norms(
+        m.ptr, _ptr(R, torch.float64, (m.n_dof,), 'R'), _ptr(free_mask, torch.uint8, (m.n_dof,), 'free_mask'),
+        n, _ptr(rnorm, torch.float64, (n,), 'rnorm'), _ptr(out, torch.float64, (3,), 'out'),
+        _stream(stream)), 'macro_residual_norms')

@@ -1,0 +1,1070 @@
+// rom_core.cuh -- device building blocks of the hyper-reduced RVE evaluation
+// (Lange, Huetter, Kiefer, arXiv 2306.02687, Sec. 3.2-3.3 and Sec. 4).
+//
+//   * compressible Neo-Hooke law P(F), A = dP/dF (the micro law of the
+//     synthetic workloads; the paper leaves the hyperelastic law open)
+//   * polar split F = R U (Sec. 3.2.2) and the derivative dR, dU
+//   * the batched evaluation kernel template (steps a1-a7 of the header)
+//
+// Kernel organisation (one CTA = NP macro points of one RVE type):
+//   for every chunk of CI ECM points
+//     stage    B rows of the chunk -> shared memory (float64 copy for the
+//              FP64-accurate kinematics, KT copy extended by the identity
+//              block [B_i | I] as left operand of the contraction)
+//     pointwise  one thread per (point, ECM point): F_i = U + B_i q, the law,
+//              w_i P_i (float64) and Y_i = w_i A_i [B_i | I] (KT) -> shared
+//     contract register-tiled  M += sum_i [B_i | I]^T Y_i, i.e. the augmented
+//              reduced system [[K, K_qF], [K_Fq, K_FF]] of Eq. ROMstiffness
+//              plus its macro coupling, and the float64 GEMV r += B_i^T w_i P_i
+//   condense one warp per point: partial Cholesky of the K block carried
+//              through the coupling block and the right-hand side [r; V0 Pbar]
+//              -- the trailing g x g block becomes V0 C_U and the trailing
+//              right-hand side V0 Pbar_alg (static condensation, Sec. 3.2.3)
+//   output   s, S, Pbar = R Pbar_alg, dPdF through the polar derivative.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "df64.cuh"
+
+namespace rverom {
+
+constexpr int ST_OK = 0, ST_DETF = 1, ST_NONSPD = 2, ST_NONFINITE = 3;
+
+__device__ __forceinline__ float kfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double kfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <int D>
+struct Dims {
+    static constexpr int G = D * D;
+    static constexpr int NS = (D == 2) ? 3 : 6;
+};
+
+// Voigt pair v -> (i, j); order 2D (11,22,12), 3D (11,22,33,12,13,23).
+__host__ __device__ inline void voigt_pair(int D, int v, int &i, int &j) {
+    if (D == 2) {
+        const int a[3] = {0, 1, 0}, b[3] = {0, 1, 1};
+        i = a[v];
+        j = b[v];
+    } else {
+        const int a[6] = {0, 1, 2, 0, 0, 1}, b[6] = {0, 1, 2, 1, 2, 2};
+        i = a[v];
+        j = b[v];
+    }
+}
+
+struct TypeDev {
+    int n, m;
+    const double *B;   // [m][g][n]
+    const float *Bh;   // [m][g][n] float32 leading part of B
+    const float *Bl;   // [m][g][n] float32 remainder B - Bh
+    const double *w;   // [m]
+    const int *phase;  // [m]
+    double mu[2], kappa[2];
+};
+
+struct EvalArgs {
+    TypeDev t;
+    int64_t n_points;
+    const int32_t *perm;    // point lists of all types (bucketed) or nullptr
+    const int32_t *count;   // device count of this type's list, or nullptr (= n_points)
+    const int32_t *offset;  // device offset of this type's list in perm
+    int nmax;
+    double V0;
+    const double *Fbar;
+    double *q, *s, *S, *Uprev;
+    double *Pbar, *dPdF, *rnorm;
+    int32_t *status;
+    // adjoint mode only
+    const double *gP;   // [n][g] cotangent on Pbar
+    double *gF;         // [n][g] cotangent on Fbar (out)
+    double *partials;   // [gridDim.x][4] per-CTA sums of the moduli gradient
+};
+
+// ---------------------------------------------------------------------------
+// small dense helpers
+template <int D>
+__device__ __forceinline__ double det(const double *F) {
+    if (D == 2) return F[0] * F[3] - F[1] * F[2];
+    return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+           F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+
+// inverse via the adjugate; returns det
+template <int D>
+__device__ __forceinline__ double inverse(const double *F, double *Fi) {
+    double J = det<D>(F);
+    double r = 1.0 / J;
+    if (D == 2) {
+        Fi[0] = F[3] * r;
+        Fi[1] = -F[1] * r;
+        Fi[2] = -F[2] * r;
+        Fi[3] = F[0] * r;
+    } else {
+        Fi[0] = (F[4] * F[8] - F[5] * F[7]) * r;
+        Fi[1] = (F[2] * F[7] - F[1] * F[8]) * r;
+        Fi[2] = (F[1] * F[5] - F[2] * F[4]) * r;
+        Fi[3] = (F[5] * F[6] - F[3] * F[8]) * r;
+        Fi[4] = (F[0] * F[8] - F[2] * F[6]) * r;
+        Fi[5] = (F[2] * F[3] - F[0] * F[5]) * r;
+        Fi[6] = (F[3] * F[7] - F[4] * F[6]) * r;
+        Fi[7] = (F[1] * F[6] - F[0] * F[7]) * r;
+        Fi[8] = (F[0] * F[4] - F[1] * F[3]) * r;
+    }
+    return J;
+}
+
+// ---------------------------------------------------------------------------
+// Neo-Hooke: P = mu F + (lam lnJ - mu) F^-T, lam = kappa - 2 mu / 3.
+// Returns false when det F <= 0 (or not finite).
+template <int D>
+__device__ __forceinline__ bool nh_stress(const double *F, double mu, double kappa, double *P,
+                                          double *Fi, double &lnJ) {
+    constexpr int G = D * D;
+    double J = inverse<D>(F, Fi);
+    if (!(J > 0.0) || !isfinite(J)) return false;
+    lnJ = log(J);
+    double lam = kappa - (2.0 / 3.0) * mu;
+    double c = lam * lnJ - mu;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) P[i * D + j] = mu * F[i * D + j] + c * Fi[j * D + i];
+    (void)G;
+    return true;
+}
+
+// Row c = (i, J) of A[iJ][kL] = mu d_ik d_JL + lam Fi_Ji Fi_Lk + c3 Fi_Li Fi_Jk,
+// c3 = mu - lam lnJ; fi is F^-1 in KT precision.
+template <int D, typename KT>
+__device__ __forceinline__ void nh_tangent_row(const KT *fi, KT lam, KT c3, KT mu, int c, KT *Arow) {
+    const int i = c / D, J = c % D;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int L = 0; L < D; ++L) {
+            KT v = lam * fi[J * D + i] * fi[L * D + k] + c3 * fi[L * D + i] * fi[J * D + k];
+            if (i == k && J == L) v += mu;
+            Arow[k * D + L] = v;
+        }
+}
+
+// Neo-Hooke stress in double-float: P = mu F + ((lam lnJ - mu)/J) cof(F),
+// F^-T = cof(F)/J.  Also returns F^-1 and ln J in float32 for the tangent.
+template <int D>
+__device__ __forceinline__ bool nh_stress_df(const df *F, df mu, df lam, df *P, float *fi, float &lnJf) {
+    constexpr int G = D * D;
+    df cof[G];
+    df J;
+    if (D == 2) {
+        cof[0] = F[3];
+        cof[1] = df_neg(F[2]);
+        cof[2] = df_neg(F[1]);
+        cof[3] = F[0];
+        J = df_sub(df_mul(F[0], F[3]), df_mul(F[1], F[2]));
+    } else {
+        cof[0] = df_sub(df_mul(F[4], F[8]), df_mul(F[5], F[7]));
+        cof[1] = df_sub(df_mul(F[5], F[6]), df_mul(F[3], F[8]));
+        cof[2] = df_sub(df_mul(F[3], F[7]), df_mul(F[4], F[6]));
+        cof[3] = df_sub(df_mul(F[2], F[7]), df_mul(F[1], F[8]));
+        cof[4] = df_sub(df_mul(F[0], F[8]), df_mul(F[2], F[6]));
+        cof[5] = df_sub(df_mul(F[1], F[6]), df_mul(F[0], F[7]));
+        cof[6] = df_sub(df_mul(F[1], F[5]), df_mul(F[2], F[4]));
+        cof[7] = df_sub(df_mul(F[2], F[3]), df_mul(F[0], F[5]));
+        cof[8] = df_sub(df_mul(F[0], F[4]), df_mul(F[1], F[3]));
+        J = df_add(df_add(df_mul(F[0], cof[0]), df_mul(F[1], cof[1])), df_mul(F[2], cof[2]));
+    }
+    if (!(J.hi > 0.0f) || !isfinite(J.hi)) return false;
+    const df lnJ = df_log(J);
+    const df rJ = df_div(df{1.0f, 0.0f}, J);
+    const df coef = df_mul(df_sub(df_mul(lam, lnJ), mu), rJ);
+#pragma unroll
+    for (int c = 0; c < G; ++c) P[c] = df_add(df_mul(mu, F[c]), df_mul(coef, cof[c]));
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) fi[i * D + j] = __fmul_rn(cof[j * D + i].hi, rJ.hi);
+    lnJf = lnJ.hi;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// polar decomposition F = R U.  2D: closed form; 3D: Newton iteration
+// X <- (X + X^-T)/2 on the rotation (quadratically convergent, bounded).
+template <int D>
+__device__ bool polar(const double *F, double *R, double *U) {
+    constexpr int G = D * D;
+    if (D == 2) {
+        double a = F[0] + F[3], b = F[2] - F[1];
+        double rho = sqrt(a * a + b * b);
+        if (!(rho > 0.0)) return false;
+        double c = a / rho, s = b / rho;
+        R[0] = c;
+        R[1] = -s;
+        R[2] = s;
+        R[3] = c;
+    } else {
+        double X[G], Xi[G];
+#pragma unroll
+        for (int x = 0; x < G; ++x) X[x] = F[x];
+        for (int it = 0; it < 60; ++it) {
+            double J = inverse<3>(X, Xi);
+            if (!(J > 0.0)) return false;
+            double dmax = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    double nx = 0.5 * (X[i * 3 + j] + Xi[j * 3 + i]);
+                    dmax = fmax(dmax, fabs(nx - X[i * 3 + j]));
+                    X[i * 3 + j] = nx;
+                }
+            if (dmax <= 1e-16) break;
+        }
+#pragma unroll
+        for (int x = 0; x < G; ++x) R[x] = X[x];
+    }
+    // U = R^T F, symmetrized
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) v += R[k * D + i] * F[k * D + j];
+            U[i * D + j] = v;
+        }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i + 1; j < D; ++j) {
+            double v = 0.5 * (U[i * D + j] + U[j * D + i]);
+            U[i * D + j] = v;
+            U[j * D + i] = v;
+        }
+    return true;
+}
+
+// For dF = e_(i0,J0): Omega (skew, R^T dR) and dU (symmetric) of the polar
+// derivative, from  Omega U + U Omega = R^T dF - dF^T R.
+template <int D>
+__device__ void polar_dir(const double *R, const double *U, int i0, int J0, double *Om,
+                          double *dU) {
+    constexpr int G = D * D;
+    double X[G];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) X[a * D + b] = (b == J0) ? R[i0 * D + a] : 0.0;
+    double W[G];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) W[a * D + b] = X[a * D + b] - X[b * D + a];
+    if (D == 2) {
+        double om = W[2] / (U[0] + U[3]);
+        Om[0] = 0.0;
+        Om[1] = -om;
+        Om[2] = om;
+        Om[3] = 0.0;
+    } else {
+        // (tr U I - U) omega = axial(W)
+        double w0 = W[7], w1 = W[2], w2 = W[3];
+        double tr = U[0] + U[4] + U[8];
+        double Mx[9];
+#pragma unroll
+        for (int x = 0; x < 9; ++x) Mx[x] = -U[x];
+        Mx[0] += tr;
+        Mx[4] += tr;
+        Mx[8] += tr;
+        double Mi[9];
+        inverse<3>(Mx, Mi);
+        double o0 = Mi[0] * w0 + Mi[1] * w1 + Mi[2] * w2;
+        double o1 = Mi[3] * w0 + Mi[4] * w1 + Mi[5] * w2;
+        double o2 = Mi[6] * w0 + Mi[7] * w1 + Mi[8] * w2;
+        Om[0] = 0.0;
+        Om[1] = -o2;
+        Om[2] = o1;
+        Om[3] = o2;
+        Om[4] = 0.0;
+        Om[5] = -o0;
+        Om[6] = -o1;
+        Om[7] = o0;
+        Om[8] = 0.0;
+    }
+    // dU = X - Omega U, symmetrized
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            double v = X[a * D + b];
+#pragma unroll
+            for (int k = 0; k < D; ++k) v -= Om[a * D + k] * U[k * D + b];
+            dU[a * D + b] = v;
+        }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a + 1; b < D; ++b) {
+            double v = 0.5 * (dU[a * D + b] + dU[b * D + a]);
+            dU[a * D + b] = v;
+            dU[b * D + a] = v;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory plan of the evaluation kernel (MIX: float32 contraction with
+// double-float kinematics/law/residual; otherwise everything float64)
+template <int D, int NA, int TA, int TB, int NP, int CI, typename KT>
+struct Plan {
+    static constexpr bool MIX = std::is_same<KT, float>::value;
+    static constexpr int G = D * D;
+    static constexpr int NS = Dims<D>::NS;
+    static constexpr int NQ = NA - G;                 // largest n~ served
+    static constexpr int QP = NQ | 1;                 // odd row pitch (banks)
+    static constexpr int BP = NQ | 1;
+    static constexpr int TPP = (NA / TA) * (NA / TB); // register tiles per point
+    static constexpr int NT = NP * TPP;               // threads per CTA
+    static constexpr int KC = CI * G;                 // contraction length per chunk
+    static constexpr int RPT = (NP * NQ + NT - 1) / NT;
+    static_assert(NA % TA == 0 && NA % TB == 0, "tile must divide NA");
+    static_assert(NT % 32 == 0 && NT <= 1024, "bad thread count");
+    // 8-byte words (a double, or a double-float pair hi|lo stored as two
+    // float arrays of the same length inside the region)
+    static constexpr int o_q = 0;
+    static constexpr int o_U = o_q + NP * QP;
+    static constexpr int o_Udf = o_U + NP * G;
+    static constexpr int o_R = o_Udf + NP * G;
+    static constexpr int o_dU = o_R + NP * G;
+    static constexpr int o_r = o_dU + NP * NS;
+    static constexpr int o_PU = o_r + NP * NQ;
+    static constexpr int o_B = o_PU + NP * G;
+    static constexpr int o_WP = o_B + CI * G * BP;
+    static constexpr int o_w = o_WP + NP * CI * G;
+    static constexpr int o_y = o_w + CI;
+    static constexpr int o_X = o_y + NP * NA;
+    static constexpr int o_q64 = o_X + NP * G * NQ;   // float64 q (MIX keeps split copies in o_q)
+    static constexpr int n_dbl = o_q64 + NP * QP;
+    // ints
+    static constexpr int o_ph = 0;
+    static constexpr int o_flag = o_ph + CI;
+    static constexpr int o_pidx = o_flag + NP;
+    static constexpr int n_int = ((o_pidx + NP + 3) / 4) * 4;
+    // KT arrays
+    static constexpr int o_Bx = 0;
+    static constexpr int o_YM = o_Bx + KC * NA;
+    static constexpr int NAP = NA + 1;                 // padded Y row (bank conflicts)
+    static constexpr int n_YM = (NP * KC * NAP > NP * NA * NA) ? NP * KC * NAP : NP * NA * NA;
+    static constexpr int n_kt = o_YM + n_YM;
+    static constexpr size_t bytes = sizeof(double) * n_dbl + sizeof(int) * n_int + sizeof(KT) * n_kt;
+};
+
+// ---------------------------------------------------------------------------
+template <int D, int NA, int TA, int TB, int NP, int CI, typename KT, bool ADJ>
+__global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
+    eval_kernel(EvalArgs a) {
+    using PL = Plan<D, NA, TA, TB, NP, CI, KT>;
+    constexpr bool MIX = PL::MIX;
+    constexpr int G = PL::G, NS = PL::NS, NQ = PL::NQ, QP = PL::QP, BP = PL::BP;
+    constexpr int TPP = PL::TPP, NT = PL::NT, KC = PL::KC, RPT = PL::RPT;
+    constexpr int NTB = NA / TB;
+    constexpr int NAP = PL::NAP;
+    using XT = KT;  // precision of K^-1 K_qF (feeds S and the adjoint's z)
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *sd = reinterpret_cast<double *>(smem);
+    int *si = reinterpret_cast<int *>(sd + PL::n_dbl);
+    KT *sk = reinterpret_cast<KT *>(si + PL::n_int);
+    double *s_q = sd + PL::o_q, *s_U = sd + PL::o_U, *s_R = sd + PL::o_R, *s_dU = sd + PL::o_dU;
+    double *s_r = sd + PL::o_r, *s_PU = sd + PL::o_PU, *s_B = sd + PL::o_B, *s_WP = sd + PL::o_WP;
+    double *s_w = sd + PL::o_w, *s_y = sd + PL::o_y;
+    double *s_qd = MIX ? sd + PL::o_q64 : s_q;  // float64 amplitudes
+    XT *s_X = reinterpret_cast<XT *>(sd + PL::o_X);
+    // double-float views (MIX): hi array followed by lo array
+    float *s_qh = reinterpret_cast<float *>(s_q), *s_ql = s_qh + NP * QP;
+    float *s_Uh = reinterpret_cast<float *>(sd + PL::o_Udf), *s_Ul = s_Uh + NP * G;
+    float *s_Bh = reinterpret_cast<float *>(s_B), *s_Bl = s_Bh + CI * G * BP;
+    float *s_WPh = reinterpret_cast<float *>(s_WP), *s_WPl = s_WPh + NP * CI * G;
+    float *s_wh = reinterpret_cast<float *>(s_w), *s_wl = s_wh + CI;
+    int *s_ph = si + PL::o_ph, *s_flag = si + PL::o_flag, *s_pidx = si + PL::o_pidx;
+    KT *s_Bx = sk + PL::o_Bx, *s_Y = sk + PL::o_YM, *s_M = sk + PL::o_YM;
+
+    const int tid = threadIdx.x;
+    const int n = a.t.n, m = a.t.m;
+    const int na = n + G;
+    const int64_t count = a.count ? (int64_t)(*a.count) : a.n_points;
+    const int32_t *perm = a.perm ? a.perm + (a.offset ? *a.offset : 0) : nullptr;
+    const int64_t n_tiles = (count + NP - 1) / NP;
+
+    // register tile of the contraction
+    const int tp = tid / TPP;
+    const int tt = tid % TPP;
+    const int a0 = (tt / NTB) * TA, b0 = (tt % NTB) * TB;
+    double th[4] = {0.0, 0.0, 0.0, 0.0};  // adjoint: (mu, kappa) of phase 0, phase 1
+    // material constants in double-float
+    df dmu0{0.0f, 0.0f}, dmu1{0.0f, 0.0f}, dlam0{0.0f, 0.0f}, dlam1{0.0f, 0.0f};
+    const KT kmu0 = (KT)a.t.mu[0], kmu1 = (KT)a.t.mu[1];
+    const KT klam0 = (KT)(a.t.kappa[0] - (2.0 / 3.0) * a.t.mu[0]);
+    const KT klam1 = (KT)(a.t.kappa[1] - (2.0 / 3.0) * a.t.mu[1]);
+    if (MIX) {
+        dmu0 = df_from(a.t.mu[0]);
+        dmu1 = df_from(a.t.mu[1]);
+        dlam0 = df_from(a.t.kappa[0] - (2.0 / 3.0) * a.t.mu[0]);
+        dlam1 = df_from(a.t.kappa[1] - (2.0 / 3.0) * a.t.mu[1]);
+    }
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // ---- a1: polar split, micro update --------------------------------
+        if (tid < NP) {
+            const int p = tid;
+            int64_t li = tile * NP + p;
+            int gp = -1;
+            if (li < count) gp = perm ? perm[li] : (int)li;
+            s_pidx[p] = gp;
+            int flag = -1;
+            double F[G], R[G], U[G];
+            if (gp >= 0) {
+                flag = ST_OK;
+                bool fin = true;
+#pragma unroll
+                for (int c = 0; c < G; ++c) {
+                    F[c] = a.Fbar[(int64_t)gp * G + c];
+                    fin = fin && isfinite(F[c]);
+                }
+                if (!fin) flag = ST_NONFINITE;
+                else if (!(det<D>(F) > 0.0) || !polar<D>(F, R, U)) flag = ST_DETF;
+            }
+            if (flag != ST_OK) {
+#pragma unroll
+                for (int c = 0; c < G; ++c) {
+                    R[c] = (c % (D + 1) == 0) ? 1.0 : 0.0;
+                    U[c] = R[c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                s_U[p * G + c] = U[c];
+                s_R[p * G + c] = R[c];
+                if (MIX) {
+                    const df u = df_from(U[c]);
+                    s_Uh[p * G + c] = u.hi;
+                    s_Ul[p * G + c] = u.lo;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NS; ++v) {
+                int i, j;
+                voigt_pair(D, v, i, j);
+                s_dU[p * NS + v] = (!ADJ && flag == ST_OK) ? U[i * D + j] - a.Uprev[(int64_t)gp * NS + v] : 0.0;
+            }
+            s_flag[p] = flag;
+        }
+        __syncthreads();
+        for (int x = tid; x < NP * NQ; x += NT) {
+            const int p = x / NQ, j = x % NQ;
+            const int gp = s_pidx[p];
+            double qv = 0.0;
+            if (j < n && gp >= 0 && s_flag[p] == ST_OK) {
+                const int64_t base = (int64_t)gp * a.nmax + j;
+                qv = a.q[base];
+                if (!ADJ) {
+                    qv -= a.s[base];
+#pragma unroll
+                    for (int v = 0; v < NS; ++v) qv -= a.S[base * NS + v] * s_dU[p * NS + v];
+                }
+            }
+            s_qd[p * QP + j] = qv;
+            if (MIX) {
+                const df v = df_from(qv);
+                s_qh[p * QP + j] = v.hi;
+                s_ql[p * QP + j] = v.lo;
+            }
+        }
+
+        KT acc[TA][TB];
+        KT kh[TA][TB], kc[TA][TB];  // MIX: Kahan-compensated sum of chunk partials
+#pragma unroll
+        for (int x = 0; x < TA; ++x)
+#pragma unroll
+            for (int y = 0; y < TB; ++y) {
+                acc[x][y] = (KT)0;
+                kh[x][y] = (KT)0;
+                kc[x][y] = (KT)0;
+            }
+        double racc[RPT];
+        dacc rdacc[RPT];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            racc[u] = 0.0;
+            rdacc[u] = dacc{0.0f, 0.0f};
+        }
+        double pu = 0.0;
+        df pudf = df{0.0f, 0.0f};
+        __syncthreads();
+
+        // ---- ECM loop: a2-a5 ---------------------------------------------
+        for (int i0 = 0; i0 < m; i0 += CI) {
+            // stage the chunk of the gradient table
+            for (int x = tid; x < CI * G * NQ; x += NT) {
+                const int il = x / (G * NQ), rem = x % (G * NQ), c = rem / NQ, j = rem % NQ;
+                const bool in = i0 + il < m && j < n;
+                const int64_t gi = ((int64_t)(i0 + il) * G + c) * n + j;
+                if (MIX) {
+                    s_Bh[(il * G + c) * BP + j] = in ? a.t.Bh[gi] : 0.0f;
+                    s_Bl[(il * G + c) * BP + j] = in ? a.t.Bl[gi] : 0.0f;
+                } else {
+                    s_B[(il * G + c) * BP + j] = in ? a.t.B[gi] : 0.0;
+                }
+            }
+            for (int x = tid; x < KC * NA; x += NT) {
+                const int k = x / NA, col = x % NA, il = k / G, c = k % G;
+                KT v = (KT)0;
+                if (i0 + il < m) {
+                    const int64_t gi = ((int64_t)(i0 + il) * G + c) * n + col;
+                    if (col < n) v = MIX ? (KT)a.t.Bh[gi] : (KT)a.t.B[gi];
+                    else if (col - n == c) v = (KT)1;
+                }
+                s_Bx[x] = v;
+            }
+            if (tid < CI) {
+                const bool ok = i0 + tid < m;
+                const double wv = ok ? a.t.w[i0 + tid] : 0.0;
+                if (MIX) {
+                    const df w2 = df_from(wv);
+                    s_wh[tid] = w2.hi;
+                    s_wl[tid] = w2.lo;
+                } else {
+                    s_w[tid] = wv;
+                }
+                s_ph[tid] = ok ? a.t.phase[i0 + tid] : 0;
+            }
+            __syncthreads();
+
+            // pointwise: F_i, law, w P_i, Y_i = w A_i [B_i | I]
+            for (int task = tid; task < NP * CI; task += NT) {
+                const int p = task % NP, il = task / NP;
+                KT *yrow = s_Y + ((il * G) * NP + p) * NAP;  // row k = il*G + c at yrow + c*NP*NAP
+                bool live = (s_flag[p] == ST_OK) && (i0 + il < m);
+                const int ph = s_ph[il];
+                KT fi[G];
+                KT lnJk = (KT)0;
+                if (live) {
+                    if (MIX) {
+                        df F[G], P[G];
+                        const float *Bh = s_Bh + il * G * BP, *Bl = s_Bl + il * G * BP;
+                        const float *qh = s_qh + p * QP, *ql = s_ql + p * QP;
+                        dacc sacc[G];
+#pragma unroll
+                        for (int c = 0; c < G; ++c) sacc[c] = dacc{s_Uh[p * G + c], s_Ul[p * G + c]};
+                        for (int j = 0; j < n; ++j) {
+                            const float qhj = qh[j], qlj = ql[j];
+#pragma unroll
+                            for (int c = 0; c < G; ++c) dacc_fma(sacc[c], Bh[c * BP + j], Bl[c * BP + j], qhj, qlj);
+                        }
+#pragma unroll
+                        for (int c = 0; c < G; ++c) F[c] = dacc_get(sacc[c]);
+                        float lnf;
+                        float fif[G];
+                        if (!nh_stress_df<D>(F, ph ? dmu1 : dmu0, ph ? dlam1 : dlam0, P, fif, lnf)) {
+                            atomicCAS(&s_flag[p], ST_OK, ST_DETF);
+                            live = false;
+                        } else {
+                            const df w2{s_wh[il], s_wl[il]};
+#pragma unroll
+                            for (int c = 0; c < G; ++c) {
+                                const df wp = df_mul(w2, P[c]);
+                                s_WPh[(il * G + c) * NP + p] = wp.hi;
+                                s_WPl[(il * G + c) * NP + p] = wp.lo;
+                                fi[c] = (KT)fif[c];
+                            }
+                            lnJk = (KT)lnf;
+                        }
+                    } else {
+                        double F[G], P[G], Fi[G], lnJ = 0.0;
+                        const double *Bi = s_B + il * G * BP;
+                        const double *qp = s_q + p * QP;
+#pragma unroll
+                        for (int c = 0; c < G; ++c) F[c] = s_U[p * G + c];
+                        for (int j = 0; j < n; ++j) {
+                            const double qj = qp[j];
+#pragma unroll
+                            for (int c = 0; c < G; ++c) F[c] = fma(Bi[c * BP + j], qj, F[c]);
+                        }
+                        if (!nh_stress<D>(F, a.t.mu[ph], a.t.kappa[ph], P, Fi, lnJ)) {
+                            atomicCAS(&s_flag[p], ST_OK, ST_DETF);
+                            live = false;
+                        } else {
+                            const double wi = s_w[il];
+#pragma unroll
+                            for (int c = 0; c < G; ++c) {
+                                s_WP[(il * G + c) * NP + p] = wi * P[c];
+                                fi[c] = (KT)Fi[c];
+                            }
+                            lnJk = (KT)lnJ;
+                        }
+                    }
+                }
+                if (live) {
+                    const KT muk = ph ? kmu1 : kmu0, lam = ph ? klam1 : klam0;
+                    const KT c3 = muk - lam * lnJk;
+                    const KT *Bx = s_Bx + il * G * NA;
+                    const KT wk = MIX ? (KT)s_wh[il] : (KT)s_w[il];
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        KT Ar[G];
+                        nh_tangent_row<D, KT>(fi, lam, c3, muk, c, Ar);
+                        KT *yr = yrow + c * NP * NAP;
+                        for (int b = 0; b < n; ++b) {
+                            KT v = (KT)0;
+#pragma unroll
+                            for (int c2 = 0; c2 < G; ++c2) v = kfma(Ar[c2], Bx[c2 * NA + b], v);
+                            yr[b] = wk * v;
+                        }
+#pragma unroll
+                        for (int c2 = 0; c2 < G; ++c2) yr[n + c2] = wk * Ar[c2];
+                        for (int b = na; b < NA; ++b) yr[b] = (KT)0;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        if (MIX) {
+                            s_WPh[(il * G + c) * NP + p] = 0.0f;
+                            s_WPl[(il * G + c) * NP + p] = 0.0f;
+                        } else {
+                            s_WP[(il * G + c) * NP + p] = 0.0;
+                        }
+                        KT *yr = yrow + c * NP * NAP;
+                        for (int b = 0; b < NA; ++b) yr[b] = (KT)0;
+                    }
+                }
+            }
+            __syncthreads();
+
+            // contraction of the augmented system (register tiles)
+            {
+                const KT *Yp = s_Y + tp * NAP + b0;
+#pragma unroll 4
+                for (int k = 0; k < KC; ++k) {
+                    KT av[TA], bv[TB];
+#pragma unroll
+                    for (int x = 0; x < TA; ++x) av[x] = s_Bx[k * NA + a0 + x];
+#pragma unroll
+                    for (int y = 0; y < TB; ++y) bv[y] = Yp[k * NP * NAP + y];
+#pragma unroll
+                    for (int x = 0; x < TA; ++x)
+#pragma unroll
+                        for (int y = 0; y < TB; ++y) acc[x][y] = kfma(av[x], bv[y], acc[x][y]);
+                }
+                if (MIX) {
+                    // fold the chunk partial into the compensated sum
+#pragma unroll
+                    for (int x = 0; x < TA; ++x)
+#pragma unroll
+                        for (int y = 0; y < TB; ++y) {
+                            const float yv = __fsub_rn(acc[x][y], kc[x][y]);
+                            const float t = __fadd_rn(kh[x][y], yv);
+                            kc[x][y] = __fsub_rn(__fsub_rn(t, kh[x][y]), yv);
+                            kh[x][y] = t;
+                            acc[x][y] = 0.0f;
+                        }
+                }
+            }
+            // float64-accurate reduced residual and homogenized stress
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                const int o = tid + u * NT;
+                if (o < NP * NQ) {
+                    const int p = o / NQ, j = o % NQ;
+                    if (j < n) {
+                        if (MIX) {
+                            dacc v = rdacc[u];
+                            for (int il = 0; il < CI; ++il)
+#pragma unroll
+                                for (int c = 0; c < G; ++c) {
+                                    const int bi = (il * G + c) * BP + j, wi = (il * G + c) * NP + p;
+                                    dacc_fma(v, s_Bh[bi], s_Bl[bi], s_WPh[wi], s_WPl[wi]);
+                                }
+                            rdacc[u] = v;
+                        } else {
+                            double v = racc[u];
+                            for (int il = 0; il < CI; ++il)
+#pragma unroll
+                                for (int c = 0; c < G; ++c)
+                                    v = fma(s_B[(il * G + c) * BP + j], s_WP[(il * G + c) * NP + p], v);
+                            racc[u] = v;
+                        }
+                    }
+                }
+            }
+            if (tid < NP * G) {
+                const int p = tid / G, c = tid % G;
+                for (int il = 0; il < CI; ++il) {
+                    if (MIX) pudf = df_add(pudf, df{s_WPh[(il * G + c) * NP + p], s_WPl[(il * G + c) * NP + p]});
+                    else pu += s_WP[(il * G + c) * NP + p];
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- spill accumulators for the condensation ----------------------
+#pragma unroll
+        for (int x = 0; x < TA; ++x)
+#pragma unroll
+            for (int y = 0; y < TB; ++y)
+                s_M[(tp * NA + a0 + x) * NA + b0 + y] = MIX ? (KT)(kh[x][y] - kc[x][y]) : acc[x][y];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int o = tid + u * NT;
+            if (o < NP * NQ) s_r[o] = MIX ? df_to(dacc_get(rdacc[u])) : racc[u];
+        }
+        if (tid < NP * G) s_PU[tid] = MIX ? df_to(pudf) : pu;
+        __syncthreads();
+        // ---- a6: condensation, one warp per point --------------------------
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int p = warp; p < NP; p += NT / 32) {
+            if (s_flag[p] != ST_OK) continue;
+            KT *M = s_M + p * NA * NA;
+            double *y = s_y + p * NA;
+            for (int i = lane; i < na; i += 32) y[i] = (i < n) ? s_r[p * NQ + i] : s_PU[p * G + i - n];
+            bool fin = true;
+            for (int i = lane; i < n; i += 32) fin = fin && isfinite(s_r[p * NQ + i]);
+            fin = __all_sync(0xffffffffu, fin);
+            if (!fin) {
+                if (lane == 0) s_flag[p] = ST_NONFINITE;
+                continue;
+            }
+            __syncwarp();
+            bool spd = true;
+            for (int k = 0; k < n; ++k) {
+                const KT piv = M[k * NA + k];
+                if (!(piv > (KT)0) || !isfinite((double)piv)) {
+                    spd = false;
+                    break;
+                }
+                const KT lkk = sqrt(piv);
+                const KT inv = (KT)1 / lkk;
+                const double yk = y[k] / (double)lkk;
+                __syncwarp();
+                for (int i = k + 1 + lane; i < na; i += 32) {
+                    const KT lik = M[i * NA + k] * inv;
+                    M[i * NA + k] = lik;
+                    y[i] -= (double)lik * yk;
+                }
+                if (lane == 0) {
+                    M[k * NA + k] = lkk;
+                    y[k] = yk;
+                }
+                __syncwarp();
+                for (int i = k + 1; i < na; ++i) {
+                    const KT lik = M[i * NA + k];
+                    for (int j = k + 1 + lane; j <= i; j += 32) M[i * NA + j] -= lik * M[j * NA + k];
+                }
+                __syncwarp();
+            }
+            if (!spd) {
+                if (lane == 0) s_flag[p] = ST_NONSPD;
+                continue;
+            }
+            // s = L^-T y[0:n)  and  X = L^-T Z^T,  Z = rows n.. of the factor
+            XT *X = s_X + p * G * NQ;
+            for (int x = lane; x < G * n; x += 32) {
+                const int c = x / n, j = x % n;
+                X[c * NQ + j] = (XT)M[(n + c) * NA + j];
+            }
+            __syncwarp();
+            for (int k = n - 1; k >= 0; --k) {
+                const double lkk = (double)M[k * NA + k];
+                const double sk = y[k] / lkk;
+                XT xk[G];
+                const XT lkx = (XT)M[k * NA + k];
+#pragma unroll
+                for (int c = 0; c < G; ++c) xk[c] = X[c * NQ + k] / lkx;
+                __syncwarp();
+                for (int i = lane; i < k; i += 32) {
+                    const KT lki = M[k * NA + i];
+                    y[i] -= (double)lki * sk;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) X[c * NQ + i] -= (XT)lki * xk[c];
+                }
+                if (lane == 0) {
+                    y[k] = sk;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) X[c * NQ + k] = xk[c];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+
+        // ---- a7: outputs ---------------------------------------------------
+        for (int p = warp; p < NP && !ADJ; p += NT / 32) {
+            const int gp = s_pidx[p];
+            if (gp < 0) continue;
+            const int flag = s_flag[p];
+            const double *y = s_y + p * NA;
+            const XT *X = s_X + p * G * NQ;
+            const KT *M = s_M + p * NA * NA;
+            if (flag == ST_OK) {
+                for (int j = lane; j < a.nmax; j += 32) {
+                    const int64_t base = (int64_t)gp * a.nmax + j;
+                    const bool in = j < n;
+                    a.q[base] = in ? s_qd[p * QP + j] : 0.0;
+                    a.s[base] = in ? y[j] : 0.0;
+#pragma unroll
+                    for (int v = 0; v < NS; ++v) {
+                        int i1, j1;
+                        voigt_pair(D, v, i1, j1);
+                        double sv = 0.0;
+                        if (in) sv = (i1 == j1) ? (double)X[(i1 * D + j1) * NQ + j]
+                                                : (double)X[(i1 * D + j1) * NQ + j] + (double)X[(j1 * D + i1) * NQ + j];
+                        a.S[base * NS + v] = sv;
+                    }
+                }
+                double rmax = 0.0;
+                for (int j = lane; j < n; j += 32) rmax = fmax(rmax, fabs(s_r[p * NQ + j]));
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+                if (lane == 0) {
+                    a.rnorm[gp] = rmax;
+                    a.status[gp] = ST_OK;
+                    const double iV = 1.0 / a.V0;
+                    double Pa[G], R[G], U[G], CU[G * G];
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        Pa[c] = y[n + c] * iV;
+                        R[c] = s_R[p * G + c];
+                        U[c] = s_U[p * G + c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < G; ++c)
+#pragma unroll
+                        for (int e = 0; e < G; ++e) {
+                            const int hi = c > e ? c : e, lo = c > e ? e : c;
+                            CU[c * G + e] = (double)M[(n + hi) * NA + n + lo] * iV;
+                        }
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int J = 0; J < D; ++J) {
+                            double v = 0.0;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) v += R[i * D + k] * Pa[k * D + J];
+                            a.Pbar[(int64_t)gp * G + i * D + J] = v;
+                        }
+#pragma unroll
+                    for (int i0 = 0; i0 < D; ++i0)
+#pragma unroll
+                        for (int J0 = 0; J0 < D; ++J0) {
+                            double Om[G], dU[G], T[G];
+                            polar_dir<D>(R, U, i0, J0, Om, dU);
+                            // T = Omega Pa + C_U dU
+#pragma unroll
+                            for (int c = 0; c < G; ++c) {
+                                double v = 0.0;
+#pragma unroll
+                                for (int e = 0; e < G; ++e) v += CU[c * G + e] * dU[e];
+                                T[c] = v;
+                            }
+#pragma unroll
+                            for (int i = 0; i < D; ++i)
+#pragma unroll
+                                for (int J = 0; J < D; ++J) {
+                                    double v = T[i * D + J];
+#pragma unroll
+                                    for (int k = 0; k < D; ++k) v += Om[i * D + k] * Pa[k * D + J];
+                                    T[i * D + J] = v;
+                                }
+#pragma unroll
+                            for (int i = 0; i < D; ++i)
+#pragma unroll
+                                for (int J = 0; J < D; ++J) {
+                                    double v = 0.0;
+#pragma unroll
+                                    for (int k = 0; k < D; ++k) v += R[i * D + k] * T[k * D + J];
+                                    a.dPdF[((int64_t)gp * G + i * D + J) * G + i0 * D + J0] = v;
+                                }
+                        }
+#pragma unroll
+                    for (int v = 0; v < NS; ++v) {
+                        int i1, j1;
+                        voigt_pair(D, v, i1, j1);
+                        a.Uprev[(int64_t)gp * NS + v] = U[i1 * D + j1];
+                    }
+                }
+            } else if (lane == 0) {
+                a.status[gp] = flag;
+                a.rnorm[gp] = __longlong_as_double(0x7ff8000000000000ll);
+                for (int c = 0; c < G; ++c) a.Pbar[(int64_t)gp * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+                for (int c = 0; c < G * G; ++c) a.dPdF[(int64_t)gp * G * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+            }
+        }
+        if (ADJ) {
+            // cotangent on Fbar through the condensed tangent, and z = K^-1 K_qF R^T gP
+            for (int p = warp; p < NP; p += NT / 32) {
+                const int gp = s_pidx[p];
+                if (gp < 0) continue;
+                const int flag = s_flag[p];
+                double *y = s_y + p * NA;
+                const XT *X = s_X + p * G * NQ;
+                const KT *M = s_M + p * NA * NA;
+                if (flag != ST_OK) {
+                    if (lane == 0) {
+                        a.status[gp] = flag;
+                        for (int c = 0; c < G; ++c) a.gF[(int64_t)gp * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+                        for (int c = 0; c < G; ++c) s_PU[p * G + c] = 0.0;
+                    }
+                    for (int j = lane; j < NQ; j += 32) y[j] = 0.0;
+                    continue;
+                }
+                double gPU[G];
+                {
+                    double gPv[G], R[G];
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        gPv[c] = a.gP[(int64_t)gp * G + c];
+                        R[c] = s_R[p * G + c];
+                    }
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int J = 0; J < D; ++J) {
+                            double v = 0.0;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) v += R[k * D + i] * gPv[k * D + J];
+                            gPU[i * D + J] = v;
+                        }
+                    if (lane == 0) {
+                        a.status[gp] = ST_OK;
+                        const double iV = 1.0 / a.V0;
+                        double Pa[G], U[G], CU[G * G];
+#pragma unroll
+                        for (int c = 0; c < G; ++c) {
+                            Pa[c] = y[n + c] * iV;
+                            U[c] = s_U[p * G + c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < G; ++c)
+#pragma unroll
+                            for (int e = 0; e < G; ++e) {
+                                const int hi = c > e ? c : e, lo = c > e ? e : c;
+                                CU[c * G + e] = (double)M[(n + hi) * NA + n + lo] * iV;
+                            }
+                        // gF[e] = sum_c dPdF[c][e] gP[c], column e from the polar derivative
+#pragma unroll
+                        for (int i0 = 0; i0 < D; ++i0)
+#pragma unroll
+                            for (int J0 = 0; J0 < D; ++J0) {
+                                double Om[G], dU[G], T[G];
+                                polar_dir<D>(R, U, i0, J0, Om, dU);
+#pragma unroll
+                                for (int c = 0; c < G; ++c) {
+                                    double v = 0.0;
+#pragma unroll
+                                    for (int e = 0; e < G; ++e) v += CU[c * G + e] * dU[e];
+                                    T[c] = v;
+                                }
+#pragma unroll
+                                for (int i = 0; i < D; ++i)
+#pragma unroll
+                                    for (int J = 0; J < D; ++J) {
+                                        double v = T[i * D + J];
+#pragma unroll
+                                        for (int k = 0; k < D; ++k) v += Om[i * D + k] * Pa[k * D + J];
+                                        T[i * D + J] = v;
+                                    }
+                                // <gP, R T> = <R^T gP, T>
+                                double v = 0.0;
+#pragma unroll
+                                for (int c = 0; c < G; ++c) v += gPU[c] * T[c];
+                                a.gF[(int64_t)gp * G + i0 * D + J0] = v;
+                            }
+                    }
+                }
+                __syncwarp();
+                // z_j = sum_c X[c][j] gPU[c]  (stored over y[0:n))
+                for (int j = lane; j < NQ; j += 32) {
+                    double v = 0.0;
+                    if (j < n)
+#pragma unroll
+                        for (int c = 0; c < G; ++c) v += (double)X[c * NQ + j] * gPU[c];
+                    y[j] = v;
+                }
+                if (lane == 0)
+#pragma unroll
+                    for (int c = 0; c < G; ++c) s_PU[p * G + c] = gPU[c];
+            }
+            __syncthreads();
+            // second pass over the ECM points: (1/V0) w_i <gPU - B_i z, dP_i/dtheta>
+            for (int i0 = 0; i0 < m; i0 += CI) {
+                for (int x = tid; x < CI * G * NQ; x += NT) {
+                    const int il = x / (G * NQ), rem = x % (G * NQ), c = rem / NQ, j = rem % NQ;
+                    double v = 0.0;
+                    if (i0 + il < m && j < n) v = a.t.B[((int64_t)(i0 + il) * G + c) * n + j];
+                    s_B[(il * G + c) * BP + j] = v;
+                }
+                if (tid < CI) {
+                    const bool ok = i0 + tid < m;
+                    s_w[tid] = ok ? a.t.w[i0 + tid] : 0.0;
+                    s_ph[tid] = ok ? a.t.phase[i0 + tid] : 0;
+                }
+                __syncthreads();
+                for (int task = tid; task < NP * CI; task += NT) {
+                    const int p = task % NP, il = task / NP;
+                    if (s_flag[p] != ST_OK || i0 + il >= m) continue;
+                    const double *Bi = s_B + il * G * BP;
+                    const double *qp = s_qd + p * QP;
+                    const double *zp = s_y + p * NA;
+                    double F[G], Fi[G], v[G];
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        double f = s_U[p * G + c], bz = 0.0;
+                        for (int j = 0; j < n; ++j) {
+                            f = fma(Bi[c * BP + j], qp[j], f);
+                            bz = fma(Bi[c * BP + j], zp[j], bz);
+                        }
+                        F[c] = f;
+                        v[c] = s_PU[p * G + c] - bz;
+                    }
+                    const double J = inverse<D>(F, Fi);
+                    const double lnJ = log(J);
+                    double dmu = 0.0, dka = 0.0;
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int Jc = 0; Jc < D; ++Jc) {
+                            const double fit = Fi[Jc * D + i];
+                            const double vc = v[i * D + Jc];
+                            dmu += vc * (F[i * D + Jc] - fit - (2.0 / 3.0) * lnJ * fit);
+                            dka += vc * (lnJ * fit);
+                        }
+                    const double wv = s_w[il] / a.V0;
+                    const int ph = s_ph[il];
+                    th[2 * ph] += wv * dmu;
+                    th[2 * ph + 1] += wv * dka;
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+    if (ADJ) {
+        // deterministic block reduction of the moduli gradient into partials
+        double *red = reinterpret_cast<double *>(smem);
+        for (int k = 0; k < 4; ++k) {
+            double v = th[k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if ((tid & 31) == 0) red[(tid >> 5) * 4 + k] = v;
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double v = 0.0;
+            for (int w = 0; w < NT / 32; ++w) v += red[w * 4 + tid];
+            a.partials[(int64_t)blockIdx.x * 4 + tid] = v;
+        }
+    }
+}
+
+}  // namespace rverom

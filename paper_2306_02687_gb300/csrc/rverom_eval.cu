@@ -1,0 +1,245 @@
+// rverom_eval.cu -- handle management and the batched hyper-ROM evaluation
+// entry point (rve_rom_create / rve_rom_destroy / rve_rom_eval_batch).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rverom.h"
+#include "rom_core.cuh"
+#include "rverom_internal.h"
+
+using namespace rverom;
+
+namespace rverom {
+
+// ---------------------------------------------------------------------------
+// bucketing of a mixed-type batch: counts, offsets and a point list per type
+__global__ void bucket_count(const int32_t *type, int64_t n, int n_types, int32_t *counts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int t = type[i];
+        if (t < 0 || t >= n_types) t = n_types;
+        atomicAdd(&counts[t], 1);
+    }
+}
+
+__global__ void bucket_offsets(int n_types, const int32_t *counts, int32_t *offsets, int32_t *cursor) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int32_t o = 0;
+        for (int t = 0; t <= n_types; ++t) {
+            offsets[t] = o;
+            cursor[t] = o;
+            o += counts[t];
+        }
+    }
+}
+
+__global__ void bucket_scatter(const int32_t *type, int64_t n, int n_types, int32_t *cursor, int32_t *perm,
+                               int32_t *status, double *rnorm) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int t = type[i];
+        if (t < 0 || t >= n_types) {
+            status[i] = ST_NONFINITE;
+            if (rnorm) rnorm[i] = __longlong_as_double(0x7ff8000000000000ll);
+            t = n_types;
+        }
+        perm[atomicAdd(&cursor[t], 1)] = (int32_t)i;
+    }
+}
+
+bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) || (dim == 3 && n <= 47)); }
+
+}  // namespace rverom
+
+// ---------------------------------------------------------------------------
+extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_desc *types, double V0,
+                              rverom_t *out) {
+    if (!out) return RVEROM_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || n_types < 1 || n_types > RVEROM_MAX_TYPES || !types || !(V0 > 0.0))
+        return RVEROM_ERR_ARG;
+    const int g = dim * dim;
+    for (int t = 0; t < n_types; ++t) {
+        const rverom_type_desc &d = types[t];
+        if (d.n_ecm < 1 || !d.B || !d.w || !d.phase) return RVEROM_ERR_ARG;
+        if (!supported_modes(dim, d.n_modes)) return RVEROM_ERR_UNSUPPORTED;
+        for (int i = 0; i < d.n_ecm; ++i)
+            if (d.phase[i] < 0 || d.phase[i] > 1) return RVEROM_ERR_ARG;
+    }
+    rverom_s *h = new (std::nothrow) rverom_s();
+    if (!h) return RVEROM_ERR_ARG;
+    h->dim = dim;
+    h->n_types = n_types;
+    h->V0 = V0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete h;
+        return RVEROM_ERR_CUDA;
+    }
+    h->device = dev;
+    for (int t = 0; t < n_types; ++t) {
+        const rverom_type_desc &d = types[t];
+        TypeDev &td = h->types[t];
+        td.n = d.n_modes;
+        td.m = d.n_ecm;
+        size_t nb = (size_t)d.n_ecm * g * d.n_modes;
+        double *B = nullptr, *w = nullptr;
+        float *Bh = nullptr, *Bl = nullptr;
+        int *ph = nullptr;
+        std::vector<float> hh(nb), ll(nb);
+        for (size_t x = 0; x < nb; ++x) {
+            hh[x] = (float)d.B[x];
+            ll[x] = (float)(d.B[x] - (double)hh[x]);
+        }
+        bool ok = cudaMalloc(&B, nb * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&Bh, nb * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&Bl, nb * sizeof(float)) == cudaSuccess &&
+                  cudaMemcpy(Bh, hh.data(), nb * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(Bl, ll.data(), nb * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMalloc(&w, d.n_ecm * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&ph, d.n_ecm * sizeof(int)) == cudaSuccess &&
+                  cudaMemcpy(B, d.B, nb * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(w, d.w, d.n_ecm * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(ph, d.phase, d.n_ecm * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+        td.B = B;
+        td.Bh = Bh;
+        td.Bl = Bl;
+        td.w = w;
+        td.phase = ph;
+        for (int k = 0; k < 2; ++k) {
+            td.mu[k] = d.moduli[k][0];
+            td.kappa[k] = d.moduli[k][1];
+        }
+        if (!ok) {
+            cudaFree(B);
+            cudaFree(Bh);
+            cudaFree(Bl);
+            cudaFree(w);
+            cudaFree(ph);
+            td.Bh = nullptr;
+            td.Bl = nullptr;
+            td.B = nullptr;
+            td.w = nullptr;
+            td.phase = nullptr;
+            rve_rom_destroy(h);
+            return RVEROM_ERR_CUDA;
+        }
+        if (d.n_modes > h->nmax) h->nmax = d.n_modes;
+    }
+    if (cudaMalloc(&h->bucket_small, 4 * (RVEROM_MAX_TYPES + 1) * sizeof(int32_t)) != cudaSuccess) {
+        rve_rom_destroy(h);
+        return RVEROM_ERR_CUDA;
+    }
+    *out = h;
+    return RVEROM_OK;
+}
+
+extern "C" int rve_rom_destroy(rverom_t h) {
+    if (!h) return RVEROM_ERR_ARG;
+    cudaDeviceSynchronize();
+    for (int t = 0; t < h->n_types; ++t) {
+        cudaFree((void *)h->types[t].B);
+        cudaFree((void *)h->types[t].Bh);
+        cudaFree((void *)h->types[t].Bl);
+        cudaFree((void *)h->types[t].w);
+        cudaFree((void *)h->types[t].phase);
+    }
+    cudaFree(h->bucket_small);
+    cudaFree(h->perm);
+    cudaFree(h->partials);
+    delete h;
+    return RVEROM_OK;
+}
+
+extern "C" int rve_rom_set_moduli(rverom_t h, int32_t type, const double *moduli) {
+    if (!h || !moduli || type < 0 || type >= h->n_types) return RVEROM_ERR_ARG;
+    for (int k = 0; k < 2; ++k) {
+        h->types[type].mu[k] = moduli[2 * k];
+        h->types[type].kappa[k] = moduli[2 * k + 1];
+    }
+    return RVEROM_OK;
+}
+
+extern "C" int rve_rom_nmax(rverom_t h, int32_t *nmax) {
+    if (!h || !nmax) return RVEROM_ERR_ARG;
+    *nmax = h->nmax;
+    return RVEROM_OK;
+}
+
+namespace rverom {
+// Prepare the per-type point lists of a batch.  Returns the argument
+// template per type in `args` (perm/count filled), or an error code.
+int prepare_buckets(rverom_t h, int64_t n, const int32_t *type, int32_t *status, double *rnorm,
+                    cudaStream_t st) {
+    if (!type) return RVEROM_OK;
+    if (h->perm_cap < n) {
+        cudaStreamSynchronize(st);
+        cudaFree(h->perm);
+        h->perm = nullptr;
+        h->perm_cap = 0;
+        if (cudaMalloc(&h->perm, (size_t)n * sizeof(int32_t)) != cudaSuccess) return RVEROM_ERR_CUDA;
+        h->perm_cap = n;
+    }
+    int32_t *counts = h->bucket_small;
+    int32_t *offsets = counts + (RVEROM_MAX_TYPES + 1);
+    int32_t *cursor = offsets + (RVEROM_MAX_TYPES + 1);
+    if (cudaMemsetAsync(counts, 0, (RVEROM_MAX_TYPES + 1) * sizeof(int32_t), st) != cudaSuccess)
+        return RVEROM_ERR_CUDA;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4 * h->n_sm) grid = 4 * h->n_sm;
+    bucket_count<<<grid, 256, 0, st>>>(type, n, h->n_types, counts);
+    bucket_offsets<<<1, 32, 0, st>>>(h->n_types, counts, offsets, cursor);
+    bucket_scatter<<<grid, 256, 0, st>>>(type, n, h->n_types, cursor, h->perm, status, rnorm);
+    return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+}
+}  // namespace rverom
+
+extern "C" int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *type, const double *Fbar,
+                                  double *q, double *s, double *S, double *Uprev, double *Pbar, double *dPdF,
+                                  double *rnorm, int32_t *status, int32_t precision, void *stream) {
+    if (!h || n_points < 0 || n_points > INT32_MAX) return RVEROM_ERR_ARG;
+    if (precision != RVEROM_FP64 && precision != RVEROM_MIXED) return RVEROM_ERR_ARG;
+    if (n_points == 0) return RVEROM_OK;
+    if (!Fbar || !q || !s || !S || !Uprev || !Pbar || !dPdF || !rnorm || !status) return RVEROM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = prepare_buckets(h, n_points, type, status, rnorm, st);
+    if (rc != RVEROM_OK) return rc;
+    for (int t = 0; t < h->n_types; ++t) {
+        if (!type && t > 0) break;
+        EvalArgs a;
+        a.t = h->types[t];
+        a.n_points = n_points;
+        a.nmax = h->nmax;
+        a.V0 = h->V0;
+        a.Fbar = Fbar;
+        a.q = q;
+        a.s = s;
+        a.S = S;
+        a.Uprev = Uprev;
+        a.Pbar = Pbar;
+        a.dPdF = dPdF;
+        a.rnorm = rnorm;
+        a.status = status;
+        a.gP = nullptr;
+        a.gF = nullptr;
+        a.partials = nullptr;
+        if (type) {
+            a.perm = h->perm;
+            a.count = h->bucket_small + t;
+            a.offset = h->bucket_small + (RVEROM_MAX_TYPES + 1) + t;
+        } else {
+            a.perm = nullptr;
+            a.count = nullptr;
+            a.offset = nullptr;
+        }
+        int grid = 0;
+        cudaError_t e = dispatch_eval<false>(h->dim, a.t.n, precision == RVEROM_MIXED, a, h->n_sm, n_points, st, &grid);
+        if (e != cudaSuccess) return RVEROM_ERR_CUDA;
+    }
+    return RVEROM_OK;
+}
+
+template cudaError_t rverom::dispatch_eval<false>(int, int, bool, const EvalArgs &, int, int64_t, cudaStream_t, int *);

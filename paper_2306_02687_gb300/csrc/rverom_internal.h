@@ -1,0 +1,77 @@
+// rverom_internal.h -- handle layouts shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rverom.h"
+#include "rom_core.cuh"
+
+struct rverom_s {
+    int dim = 2;
+    int n_types = 0;
+    int nmax = 0;
+    int n_sm = 1;
+    int device = 0;
+    double V0 = 1.0;
+    rverom::TypeDev types[RVEROM_MAX_TYPES] = {};
+    int32_t *bucket_small = nullptr;  // counts | offsets | cursor, each n_types+1
+    int32_t *perm = nullptr;          // point lists of a mixed batch
+    int64_t perm_cap = 0;
+    double *partials = nullptr;       // per-CTA partial sums of the adjoint
+    int64_t partials_cap = 0;
+};
+
+namespace rverom {
+
+// Launch one compiled tile configurations <D, NA, TA, TB, NP, CI, KT> as a
+// persistent grid of at most (SMs x resident CTAs) blocks.
+template <int D, int NA, int TA, int TB, int NP, int CI, typename KT, bool ADJ>
+cudaError_t launch_cfg(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
+    using PL = Plan<D, NA, TA, TB, NP, CI, KT>;
+    auto kern = eval_kernel<D, NA, TA, TB, NP, CI, KT, ADJ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PL::NT, PL::bytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int64_t tiles = (max_points + NP - 1) / NP;
+    int64_t grid = (int64_t)n_sm * occ;
+    if (tiles < grid) grid = tiles;
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = (int)grid;
+    kern<<<(unsigned)grid, PL::NT, PL::bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Tile configuration per (dimension, n~ bucket, precision).
+template <bool ADJ>
+cudaError_t dispatch_eval(int dim, int n, bool mixed, const EvalArgs &a, int n_sm, int64_t max_points,
+                          cudaStream_t st, int *grid_out) {
+    if (dim == 2) {
+        if (mixed) {
+            if (n <= 12) return launch_cfg<2, 16, 4, 4, 16, 16, float, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 16) return launch_cfg<2, 20, 5, 5, 16, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 24) return launch_cfg<2, 28, 7, 7, 16, 16, float, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 32) return launch_cfg<2, 36, 9, 9, 16, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 64) return launch_cfg<2, 72, 9, 9, 4, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
+        } else {
+            if (n <= 12) return launch_cfg<2, 16, 4, 4, 16, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 16) return launch_cfg<2, 20, 5, 5, 16, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 24) return launch_cfg<2, 28, 7, 7, 8, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 32) return launch_cfg<2, 36, 9, 9, 8, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
+            if (n <= 64) return launch_cfg<2, 72, 9, 9, 2, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
+        }
+    } else if (dim == 3) {
+        if (mixed) {
+            if (n <= 47) return launch_cfg<3, 56, 7, 7, 4, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
+        } else {
+            if (n <= 47) return launch_cfg<3, 56, 7, 7, 2, 4, double, ADJ>(a, n_sm, max_points, st, grid_out);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+bool supported_modes(int dim, int n);
+int prepare_buckets(rverom_t h, int64_t n, const int32_t *type, int32_t *status, double *rnorm,
+                    cudaStream_t st);
+}  // namespace rverom

@@ -1,0 +1,339 @@
+// rverom_macro.cu -- macro level of the FE^2 step: deformation gradient at
+// the macro integration points, element residual/stiffness assembly from
+// (Pbar, dPdF) (Eq. 6 of the paper and its linearization), convergence norms.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/rverom.h"
+
+struct rverom_mesh_s {
+    int dim = 2, nen = 4, ngp = 4;
+    int64_t n_nodes = 0, n_elem = 0, n_ip = 0, n_dof = 0, nnz = 0;
+    int n_sm = 1;
+    int32_t *conn = nullptr;     // device [n_elem][nen]
+    double *dN = nullptr;        // device [n_ip][nen][d]
+    double *wJ0 = nullptr;       // device [n_ip]
+    int32_t *kmap = nullptr;     // device [n_elem][(nen d)^2] CSR index of K_e entries
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+};
+
+namespace {
+
+// isoparametric reference corners, same node order as the element connectivity
+void ref_corner(int d, int a, double *s) {
+    static const int c2[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+    static const int c3[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                 {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+    for (int k = 0; k < d; ++k) s[k] = d == 2 ? c2[a][k] : c3[a][k];
+}
+
+bool invert(int d, const double *J, double *Ji, double &det) {
+    if (d == 2) {
+        det = J[0] * J[3] - J[1] * J[2];
+        if (!(det > 0)) return false;
+        Ji[0] = J[3] / det;
+        Ji[1] = -J[1] / det;
+        Ji[2] = -J[2] / det;
+        Ji[3] = J[0] / det;
+        return true;
+    }
+    det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+    if (!(det > 0)) return false;
+    Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+    Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    return true;
+}
+
+__global__ void k_gradient(int D, int nen, int ngp, int64_t n_ip, const int32_t *conn, const double *dN,
+                           const double *u, double *Fbar) {
+    const int G = D * D;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_ip; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = p / ngp;
+        double F[9];
+        for (int c = 0; c < G; ++c) F[c] = (c % (D + 1) == 0) ? 1.0 : 0.0;
+        for (int a = 0; a < nen; ++a) {
+            const int64_t node = conn[e * nen + a];
+            for (int i = 0; i < D; ++i) {
+                const double ui = u[node * D + i];
+                for (int J = 0; J < D; ++J) F[i * D + J] += ui * dN[(p * nen + a) * D + J];
+            }
+        }
+        for (int c = 0; c < G; ++c) Fbar[p * G + c] = F[c];
+    }
+}
+
+// one thread per (element, local row (a, i)): row of R_e and K_e, summed over
+// the element's integration points, scattered with atomics
+template <int D>
+__global__ void k_assemble(int64_t n_elem, const int32_t *conn, const double *dN, const double *wJ0,
+                           const double *Pbar, const double *dPdF, const int32_t *kmap, double *R,
+                           double *Kvals) {
+    constexpr int G = D * D, NEN = 1 << D, NGP = 1 << D, ND = NEN * D;
+    const int64_t total = n_elem * ND;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = x / ND;
+        const int row = (int)(x % ND);
+        const int a = row / D, i = row % D;
+        double r = 0.0;
+        double krow[ND];
+#pragma unroll
+        for (int b = 0; b < ND; ++b) krow[b] = 0.0;
+        for (int gp = 0; gp < NGP; ++gp) {
+            const int64_t p = e * NGP + gp;
+            const double w = wJ0[p];
+            const double *dn = dN + p * NEN * D;
+#pragma unroll
+            for (int J = 0; J < D; ++J) r += w * Pbar[p * G + i * D + J] * dn[a * D + J];
+            if (Kvals) {
+                // t[kL] = w sum_J dN_a,J C[iJ][kL]
+                double t[G];
+#pragma unroll
+                for (int c = 0; c < G; ++c) t[c] = 0.0;
+#pragma unroll
+                for (int J = 0; J < D; ++J) {
+                    const double f = w * dn[a * D + J];
+                    const double *C = dPdF + (p * G + i * D + J) * G;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) t[c] += f * C[c];
+                }
+#pragma unroll
+                for (int b = 0; b < NEN; ++b)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        double v = 0.0;
+#pragma unroll
+                        for (int L = 0; L < D; ++L) v += t[k * D + L] * dn[b * D + L];
+                        krow[b * D + k] += v;
+                    }
+            }
+        }
+        const int64_t node = conn[e * NEN + a];
+        atomicAdd(&R[node * D + i], r);
+        if (Kvals) {
+            const int32_t *km = kmap + (e * ND + row) * ND;
+#pragma unroll
+            for (int b = 0; b < ND; ++b) atomicAdd(&Kvals[km[b]], krow[b]);
+        }
+    }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_norms(int64_t n_dof, const double *R, const uint8_t *free_mask, int64_t n_pts, const double *rnorm,
+                        double *out) {
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_dof; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = fabs(R[i]);
+        if (free_mask[i]) m0 = fmax(m0, v);
+        else m1 = fmax(m1, v);
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pts; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = rnorm[i];
+        m2 = (v == v) ? fmax(m2, fabs(v)) : __longlong_as_double(0x7ff0000000000000ll);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, off));
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, off));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(out + 0, m0);
+        atomic_max_nonneg(out + 1, m1);
+        atomic_max_nonneg(out + 2, m2);
+    }
+}
+
+int grid_for(int64_t work, int n_sm) {
+    int64_t g = (work + 255) / 256;
+    if (g > 8LL * n_sm) g = 8LL * n_sm;
+    return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace
+
+extern "C" int macro_mesh_create(int32_t dim, int64_t n_nodes, int64_t n_elem, const double *X, const int64_t *conn,
+                                 rverom_mesh_t *out) {
+    if (!out) return RVEROM_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || n_nodes < 1 || n_elem < 1 || !X || !conn) return RVEROM_ERR_ARG;
+    if (n_nodes * dim > INT32_MAX) return RVEROM_ERR_ARG;
+    const int d = dim, nen = 1 << d, ngp = 1 << d, nd = nen * d;
+    for (int64_t x = 0; x < n_elem * nen; ++x)
+        if (conn[x] < 0 || conn[x] >= n_nodes) return RVEROM_ERR_ARG;
+    rverom_mesh_s *m = new (std::nothrow) rverom_mesh_s();
+    if (!m) return RVEROM_ERR_ARG;
+    m->dim = d;
+    m->nen = nen;
+    m->ngp = ngp;
+    m->n_nodes = n_nodes;
+    m->n_elem = n_elem;
+    m->n_ip = n_elem * ngp;
+    m->n_dof = n_nodes * d;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    // Gauss points: lexicographic with the first reference coordinate fastest
+    const double g1 = 1.0 / std::sqrt(3.0);
+    std::vector<double> dN((size_t)m->n_ip * nen * d), wJ0((size_t)m->n_ip);
+    for (int64_t e = 0; e < n_elem; ++e) {
+        for (int gp = 0; gp < ngp; ++gp) {
+            double xi[3];
+            for (int k = 0; k < d; ++k) xi[k] = ((gp >> k) & 1) ? g1 : -g1;
+            double dNdxi[8][3];
+            for (int a = 0; a < nen; ++a) {
+                double s[3];
+                ref_corner(d, a, s);
+                for (int k = 0; k < d; ++k) {
+                    double v = s[k] / 2.0;
+                    for (int l = 0; l < d; ++l)
+                        if (l != k) v *= (1.0 + xi[l] * s[l]) / 2.0;
+                    dNdxi[a][k] = v;
+                }
+            }
+            double Jm[9] = {0}, Ji[9], det = 0;
+            for (int a = 0; a < nen; ++a) {
+                const int64_t node = conn[e * nen + a];
+                for (int I = 0; I < d; ++I)
+                    for (int k = 0; k < d; ++k) Jm[I * d + k] += X[node * d + I] * dNdxi[a][k];
+            }
+            if (!invert(d, Jm, Ji, det)) {
+                delete m;
+                return RVEROM_ERR_ARG;
+            }
+            const int64_t p = e * ngp + gp;
+            wJ0[p] = det;
+            for (int a = 0; a < nen; ++a)
+                for (int I = 0; I < d; ++I) {
+                    double v = 0.0;
+                    for (int k = 0; k < d; ++k) v += dNdxi[a][k] * Ji[k * d + I];
+                    dN[((size_t)p * nen + a) * d + I] = v;
+                }
+        }
+    }
+    // CSR pattern over DOFs node*d + i: all pairs of nodes sharing an element
+    std::vector<std::vector<int32_t>> adj((size_t)n_nodes);
+    for (int64_t e = 0; e < n_elem; ++e)
+        for (int a = 0; a < nen; ++a)
+            for (int b = 0; b < nen; ++b) adj[conn[e * nen + a]].push_back((int32_t)conn[e * nen + b]);
+    for (auto &v : adj) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    m->row_ptr.assign((size_t)m->n_dof + 1, 0);
+    for (int64_t node = 0; node < n_nodes; ++node)
+        for (int i = 0; i < d; ++i) m->row_ptr[node * d + i + 1] = (int64_t)adj[node].size() * d;
+    for (int64_t r = 0; r < m->n_dof; ++r) m->row_ptr[r + 1] += m->row_ptr[r];
+    m->nnz = m->row_ptr[m->n_dof];
+    m->col.resize((size_t)m->nnz);
+    for (int64_t node = 0; node < n_nodes; ++node)
+        for (int i = 0; i < d; ++i) {
+            int64_t o = m->row_ptr[node * d + i];
+            for (int32_t nb : adj[node])
+                for (int k = 0; k < d; ++k) m->col[o++] = nb * d + k;
+        }
+    std::vector<int32_t> kmap((size_t)n_elem * nd * nd);
+    for (int64_t e = 0; e < n_elem; ++e)
+        for (int a = 0; a < nen; ++a)
+            for (int i = 0; i < d; ++i) {
+                const int64_t node = conn[e * nen + a];
+                const auto &nb = adj[node];
+                for (int b = 0; b < nen; ++b) {
+                    const int32_t nodeb = (int32_t)conn[e * nen + b];
+                    const int64_t pos = std::lower_bound(nb.begin(), nb.end(), nodeb) - nb.begin();
+                    for (int k = 0; k < d; ++k)
+                        kmap[((size_t)e * nd + a * d + i) * nd + b * d + k] =
+                            (int32_t)(m->row_ptr[node * d + i] + pos * d + k);
+                }
+            }
+    std::vector<int32_t> conn32((size_t)n_elem * nen);
+    for (size_t x = 0; x < conn32.size(); ++x) conn32[x] = (int32_t)conn[x];
+    bool ok = cudaMalloc(&m->conn, conn32.size() * 4) == cudaSuccess &&
+              cudaMalloc(&m->dN, dN.size() * 8) == cudaSuccess && cudaMalloc(&m->wJ0, wJ0.size() * 8) == cudaSuccess &&
+              cudaMalloc(&m->kmap, kmap.size() * 4) == cudaSuccess &&
+              cudaMemcpy(m->conn, conn32.data(), conn32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(m->dN, dN.data(), dN.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(m->wJ0, wJ0.data(), wJ0.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(m->kmap, kmap.data(), kmap.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        macro_mesh_destroy(m);
+        return RVEROM_ERR_CUDA;
+    }
+    *out = m;
+    return RVEROM_OK;
+}
+
+extern "C" int macro_mesh_destroy(rverom_mesh_t m) {
+    if (!m) return RVEROM_ERR_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(m->conn);
+    cudaFree(m->dN);
+    cudaFree(m->wJ0);
+    cudaFree(m->kmap);
+    delete m;
+    return RVEROM_OK;
+}
+
+extern "C" int macro_mesh_sizes(rverom_mesh_t m, int64_t *n_ip, int64_t *n_dof, int64_t *nnz) {
+    if (!m) return RVEROM_ERR_ARG;
+    if (n_ip) *n_ip = m->n_ip;
+    if (n_dof) *n_dof = m->n_dof;
+    if (nnz) *nnz = m->nnz;
+    return RVEROM_OK;
+}
+
+extern "C" int macro_mesh_csr(rverom_mesh_t m, int64_t *row_ptr, int32_t *col) {
+    if (!m || !row_ptr || !col) return RVEROM_ERR_ARG;
+    std::copy(m->row_ptr.begin(), m->row_ptr.end(), row_ptr);
+    std::copy(m->col.begin(), m->col.end(), col);
+    return RVEROM_OK;
+}
+
+extern "C" int macro_gradient(rverom_mesh_t m, const double *u, double *Fbar, void *stream) {
+    if (!m || !u || !Fbar) return RVEROM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_gradient<<<grid_for(m->n_ip, m->n_sm), 256, 0, st>>>(m->dim, m->nen, m->ngp, m->n_ip, m->conn, m->dN, u, Fbar);
+    return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+}
+
+extern "C" int macro_assemble(rverom_mesh_t m, const double *Pbar, const double *dPdF, double *R, double *Kvals,
+                              void *stream) {
+    if (!m || !Pbar || !R) return RVEROM_ERR_ARG;
+    if (Kvals && !dPdF) return RVEROM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), st) != cudaSuccess) return RVEROM_ERR_CUDA;
+    if (Kvals && cudaMemsetAsync(Kvals, 0, m->nnz * sizeof(double), st) != cudaSuccess) return RVEROM_ERR_CUDA;
+    const int64_t work = m->n_elem * m->nen * m->dim;
+    if (m->dim == 2)
+        k_assemble<2><<<grid_for(work, m->n_sm), 256, 0, st>>>(m->n_elem, m->conn, m->dN, m->wJ0, Pbar, dPdF,
+                                                               m->kmap, R, Kvals);
+    else
+        k_assemble<3><<<grid_for(work, m->n_sm), 256, 0, st>>>(m->n_elem, m->conn, m->dN, m->wJ0, Pbar, dPdF,
+                                                               m->kmap, R, Kvals);
+    return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+}
+
+extern "C" int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_mask, int64_t n_points,
+                                    const double *rnorm, double *out, void *stream) {
+    if (!m || !R || !free_mask || !out || n_points < 0 || (n_points > 0 && !rnorm)) return RVEROM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(out, 0, 3 * sizeof(double), st) != cudaSuccess) return RVEROM_ERR_CUDA;
+    const int64_t work = m->n_dof > n_points ? m->n_dof : n_points;
+    k_norms<<<grid_for(work, m->n_sm), 256, 0, st>>>(m->n_dof, R, free_mask, n_points, rnorm, out);
+    return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+}
