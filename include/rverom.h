@@ -37,6 +37,7 @@ extern "C" {
 #define RVEROM_ERR_ARG (-1)         /* bad size, null pointer, unsupported shape */
 #define RVEROM_ERR_CUDA (-2)        /* a CUDA runtime call failed */
 #define RVEROM_ERR_UNSUPPORTED (-3) /* n~ or d outside the compiled kernels */
+#define RVEROM_ERR_SCRATCH_LIMIT (-4) /* batch larger than the static scratch of rve_rom_adjoint_static */
 
 #define RVEROM_STATUS_OK 0
 #define RVEROM_STATUS_DETF_NONPOS 1 /* det F <= 0 at some ECM point */
@@ -130,6 +131,34 @@ int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *type, const 
 int rve_rom_adjoint(rverom_t h, int64_t n_points, const int32_t *type, const double *Fbar,
                     const double *q, const double *gPbar, double *gFbar, double *gTheta,
                     int32_t *status, void *stream);
+
+/* rve_rom_adjoint_static: the same adjoint as rve_rom_adjoint (same kernel,
+ * same arguments, same results) for callers that must not allocate device
+ * memory during the call.  The paper has no counterpart; this is an
+ * interface variant of this library.  rve_rom_adjoint allocates its
+ * reduction workspace and the point lists of mixed-type batches with
+ * cudaMalloc on first use or when a batch grows.  Callers that cannot allow
+ * that -- a macro FE code calling the adjoint from per-increment material
+ * callbacks, where an allocation may synchronize the device and stall the
+ * host element loop, or a process whose device memory is reserved by
+ * another allocator -- use this entry point, which allocates nothing: its
+ * scratch is one static device array of RVEROM_STATIC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.
+ * Limits: mixed-type batches (type != NULL) of at most
+ * RVEROM_STATIC_MAX_TYPED_POINTS points; devices with at most
+ * RVEROM_STATIC_MAX_CTAS / 16 SMs.  Larger requests return
+ * RVEROM_ERR_SCRATCH_LIMIT before any work is enqueued.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array and its last contents; the call
+ * clears what must start at zero, but calls whose GPU work overlaps (other
+ * streams or threads on the same device) race on it. */
+#define RVEROM_STATIC_MAX_CTAS 4096
+#define RVEROM_STATIC_MAX_TYPED_POINTS (1 << 20)
+#define RVEROM_STATIC_SCRATCH_BYTES (RVEROM_STATIC_MAX_CTAS * 4 * 8 + 256 + RVEROM_STATIC_MAX_TYPED_POINTS * 4)
+int rve_rom_adjoint_static(rverom_t h, int64_t n_points, const int32_t *type, const double *Fbar,
+                           const double *q, const double *gPbar, double *gFbar, double *gTheta,
+                           int32_t *status, void *stream);
 
 /* Macro mesh of isoparametric Q4 (dim 2) or hex8 (dim 3) elements with 2^d
  * Gauss points each; integration point alpha = e * 2^d + gp (gp in

@@ -31,6 +31,7 @@ SIGNATURES = {
     'rve_rom_eval_batch': (c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                    c_vp, c_vp, c_int, c_vp]),
     'rve_rom_adjoint': (c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    'rve_rom_adjoint_static': (c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'macro_mesh_create': (c_int, [c_int, c_i64, c_i64, P(c_dbl), P(c_i64), P(c_vp)]),
     'macro_mesh_destroy': (c_int, [c_vp]),
     'macro_mesh_sizes': (c_int, [c_vp, P(c_i64), P(c_i64), P(c_i64)]),
@@ -59,7 +60,8 @@ def lib():
     return _lib
 
 
-ERRORS = {-1: 'RVEROM_ERR_ARG', -2: 'RVEROM_ERR_CUDA', -3: 'RVEROM_ERR_UNSUPPORTED'}
+ERRORS = {-1: 'RVEROM_ERR_ARG', -2: 'RVEROM_ERR_CUDA', -3: 'RVEROM_ERR_UNSUPPORTED',
+          -4: 'RVEROM_ERR_SCRATCH_LIMIT (batch larger than the static scratch of rve_rom_adjoint_static)'}
 
 
 def check(rc, what):

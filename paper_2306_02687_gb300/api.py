@@ -153,6 +153,21 @@ def rve_rom_adjoint(h, Fbar, q, gPbar, gFbar, gTheta, status, type=None, stream=
     _native.check(_native.lib().rve_rom_adjoint(h.ptr, n, *args, _stream(stream)), 'rve_rom_adjoint')
 
 
+def rve_rom_adjoint_static(h, Fbar, q, gPbar, gFbar, gTheta, status, type=None, stream=None):
+    """rve_rom_adjoint without any device allocation in the call, for callers
+    that must not allocate (see include/rverom.h): scratch is a static device
+    array shared by all calls; overlapping calls race on it."""
+    n = Fbar.shape[0]
+    g, nm = h.g, h.nmax
+    args = [_ptr(type, torch.int32, (n,), 'type') if type is not None else None,
+            _ptr(Fbar, torch.float64, (n, g), 'Fbar'), _ptr(q, torch.float64, (n, nm), 'q'),
+            _ptr(gPbar, torch.float64, (n, g), 'gPbar'), _ptr(gFbar, torch.float64, (n, g), 'gFbar'),
+            _ptr(gTheta, torch.float64, (h.n_types, 2, 2), 'gTheta'),
+            _ptr(status, torch.int32, (n,), 'status')]
+    _native.check(_native.lib().rve_rom_adjoint_static(h.ptr, n, *args, _stream(stream)),
+                  'rve_rom_adjoint_static')
+
+
 class MeshHandle:
     def __init__(self, ptr, dim, n_nodes, n_elem):
         self.ptr = ptr
