@@ -200,6 +200,7 @@ def main():
 
     roms = [rv.load_rom_file(p) for p in rom_paths]
     h = rv.rve_rom_create(d, roms, roms[0]['V0'])
+    tune = {prec: rv.rve_rom_autotune(h, prec, n_sample=16384).round(4).tolist() for prec in ('mixed', 'fp64')}
     mesh = rv.macro_mesh_create(X, conn)
     n = mesh.n_ip
     types = None
@@ -367,6 +368,7 @@ def main():
         "config": {"workload": args.workload + ': ' + wl['desc'], "macro_points_per_gpu": n,
                    "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                    "state": "mid-Newton (converged micro state, q perturbed by 1e-3 |q|)",
+                   "autotune_ms": tune,
                    "failed_points": bad},
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -117,6 +117,23 @@ int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *type, const 
                        double *q, double *s, double *S, double *Uprev, double *Pbar, double *dPdF,
                        double *rnorm, int32_t *status, int32_t precision, void *stream);
 
+/* Autotuner of the evaluation kernels: for every RVE type of the handle,
+ * time each compiled tile configuration (points per CTA, ECM points per
+ * chunk, warp-specialized or fused organisation) of the given precision on
+ * a synthetic batch of n_sample points (seeded small stretches, fresh state;
+ * device memory for it is allocated and freed here), keep the fastest for
+ * rve_rom_eval_batch, and optionally report the best-of-2 times in
+ * ms_out [n_types][RVEROM_MAX_CANDIDATES] (host; -1 for unused slots).
+ * Synchronous.  Without tuning, configuration 0 of each list is used. */
+#define RVEROM_MAX_CANDIDATES 4
+int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample, float *ms_out, void *stream);
+
+/* Pin the tile configuration `candidate` (0 .. n-1) of one type and
+ * precision for rve_rom_eval_batch; candidate < 0 only queries.  The number
+ * of compiled candidates is returned in *n_candidates (may be NULL). */
+int rve_rom_select_kernel(rverom_t h, int32_t type, int32_t precision, int32_t candidate,
+                          int32_t *n_candidates);
+
 /* Implicit-function adjoint at converged states (r(q*) = 0): for cotangents
  * gPbar on Pbar,
  *   gFbar = dPdF^T gPbar      (the condensed consistent tangent)

@@ -128,6 +128,26 @@ def rve_rom_set_moduli(h, type_id, moduli):
                   'rve_rom_set_moduli')
 
 
+def rve_rom_autotune(h, precision='mixed', n_sample=16384, stream=None):
+    """Time the compiled tile configurations of every RVE type on a synthetic
+    sample and keep the fastest; returns the times [n_types][candidates]
+    in ms (-1 where a type has fewer candidates)."""
+    ms = np.zeros((h.n_types, 4), dtype=np.float32)
+    _native.check(_native.lib().rve_rom_autotune(h.ptr, _PREC[precision], int(n_sample),
+                                                 ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                 _stream(stream)), 'rve_rom_autotune')
+    return ms
+
+
+def rve_rom_select_kernel(h, type_id, precision, candidate=-1):
+    """Pin a tile configuration (candidate >= 0) or just query; returns the
+    number of compiled configurations for this type and precision."""
+    nc = ctypes.c_int32()
+    _native.check(_native.lib().rve_rom_select_kernel(h.ptr, int(type_id), _PREC[precision], int(candidate),
+                                                      ctypes.byref(nc)), 'rve_rom_select_kernel')
+    return nc.value
+
+
 def rve_rom_eval_batch(h, Fbar, q, s, S, Uprev, Pbar, dPdF, rnorm, status, type=None,
                        precision='mixed', stream=None):
     n = Fbar.shape[0]

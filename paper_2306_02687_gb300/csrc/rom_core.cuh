@@ -314,6 +314,456 @@ __device__ void polar_dir(const double *R, const double *U, int i0, int J0, doub
         }
 }
 
+// 1/x to float64 accuracy without a float64 divide: float32 seed refined by
+// two Newton steps (r <- r (2 - x r)), each doubling the correct bits.
+template <typename KT>
+__device__ __forceinline__ double recip_acc(KT x) {
+    double r = (double)(1.0f / (float)x);
+    const double xd = (double)x;
+    r = r * (2.0 - xd * r);
+    r = r * (2.0 - xd * r);
+    return r;
+}
+
+// Static condensation of one point by one warp (step a6): in-place partial
+// Cholesky of the K block of the augmented system M = [[K, K_qF],[K_Fq, K_FF]]
+// (lower triangle, KT precision) carried through the coupling rows and the
+// float64 right-hand side y = [r; V0 Pbar_U]; afterwards y[0:n) = s = K^-1 r,
+// y[n:n+g) = V0 Pbar_alg, the trailing block of M is V0 C_U and X = K^-1 K_qF
+// (g columns of length n, pitch NQ).  Returns a status code.
+template <int D, int NA, int NQ, typename KT, typename XT>
+__device__ int condense_warp(KT *M, double *y, XT *X, const double *r, const double *PU, int n, int lane) {
+    constexpr int G = D * D;
+    const int na = n + G;
+    for (int i = lane; i < na; i += 32) y[i] = (i < n) ? r[i] : PU[i - n];
+    bool fin = true;
+    for (int i = lane; i < n; i += 32) fin = fin && isfinite(r[i]);
+    fin = __all_sync(0xffffffffu, fin);
+    if (!fin) return ST_NONFINITE;
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const KT piv = M[k * NA + k];
+        if (!(piv > (KT)0) || !isfinite(piv)) return ST_NONSPD;
+        const KT lkk = sqrt(piv);
+        const double dinv = recip_acc(lkk);
+        const KT inv = (KT)dinv;
+        const double yk = y[k] * dinv;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < na; i += 32) {
+            const KT lik = M[i * NA + k] * inv;
+            M[i * NA + k] = lik;
+            y[i] -= (double)lik * yk;
+        }
+        if (lane == 0) {
+            M[k * NA + k] = lkk;
+            y[k] = yk;
+        }
+        __syncwarp();
+        for (int i = k + 1; i < na; ++i) {
+            const KT lik = M[i * NA + k];
+            for (int j = k + 1 + lane; j <= i; j += 32) M[i * NA + j] -= lik * M[j * NA + k];
+        }
+        __syncwarp();
+    }
+    // s = L^-T y[0:n)  and  X = L^-T Z^T,  Z = rows n.. of the factor
+    for (int x = lane; x < G * n; x += 32) {
+        const int c = x / n, j = x % n;
+        X[c * NQ + j] = (XT)M[(n + c) * NA + j];
+    }
+    __syncwarp();
+    for (int k = n - 1; k >= 0; --k) {
+        const double dinv = recip_acc(M[k * NA + k]);
+        const double sk = y[k] * dinv;
+        XT xk[G];
+        const XT xinv = (XT)dinv;
+#pragma unroll
+        for (int c = 0; c < G; ++c) xk[c] = X[c * NQ + k] * xinv;
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) {
+            const KT lki = M[k * NA + i];
+            y[i] -= (double)lki * sk;
+#pragma unroll
+            for (int c = 0; c < G; ++c) X[c * NQ + i] -= (XT)lki * xk[c];
+        }
+        if (lane == 0) {
+            y[k] = sk;
+#pragma unroll
+            for (int c = 0; c < G; ++c) X[c * NQ + k] = xk[c];
+        }
+        __syncwarp();
+    }
+    return ST_OK;
+}
+
+// Outputs of one point by one warp (step a7): new state q, s, S, Uprev, the
+// rotated algorithmic stress Pbar = R Pbar_alg, the consistent tangent
+// dPbar/dFbar through the polar derivative, rnorm and status; NaN stress and
+// tangent for failed points (their state is left untouched).
+template <int D, int NA, int NQ, typename KT, typename XT>
+__device__ void write_outputs_warp(const EvalArgs &a, int gp, int flag, int n, const double *y, const XT *X,
+                                   const KT *M, const double *qd, const double *r, const double *Rm,
+                                   const double *Um, int lane) {
+    constexpr int G = D * D, NS = Dims<D>::NS;
+    if (flag == ST_OK) {
+        for (int j = lane; j < a.nmax; j += 32) {
+            const int64_t base = (int64_t)gp * a.nmax + j;
+            const bool in = j < n;
+            a.q[base] = in ? qd[j] : 0.0;
+            a.s[base] = in ? y[j] : 0.0;
+#pragma unroll
+            for (int v = 0; v < NS; ++v) {
+                int i1, j1;
+                voigt_pair(D, v, i1, j1);
+                double sv = 0.0;
+                if (in) sv = (i1 == j1) ? (double)X[(i1 * D + j1) * NQ + j]
+                                        : (double)X[(i1 * D + j1) * NQ + j] + (double)X[(j1 * D + i1) * NQ + j];
+                a.S[base * NS + v] = sv;
+            }
+        }
+        double rmax = 0.0;
+        for (int j = lane; j < n; j += 32) rmax = fmax(rmax, fabs(r[j]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+        if (lane == 0) {
+            a.rnorm[gp] = rmax;
+            a.status[gp] = ST_OK;
+            const double iV = 1.0 / a.V0;
+            double Pa[G], R[G], U[G], CU[G * G];
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                Pa[c] = y[n + c] * iV;
+                R[c] = Rm[c];
+                U[c] = Um[c];
+            }
+#pragma unroll
+            for (int c = 0; c < G; ++c)
+#pragma unroll
+                for (int e = 0; e < G; ++e) {
+                    const int hi = c > e ? c : e, lo = c > e ? e : c;
+                    CU[c * G + e] = (double)M[(n + hi) * NA + n + lo] * iV;
+                }
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int J = 0; J < D; ++J) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) v += R[i * D + k] * Pa[k * D + J];
+                    a.Pbar[(int64_t)gp * G + i * D + J] = v;
+                }
+#pragma unroll
+            for (int i0 = 0; i0 < D; ++i0)
+#pragma unroll
+                for (int J0 = 0; J0 < D; ++J0) {
+                    double Om[G], dU[G], T[G];
+                    polar_dir<D>(R, U, i0, J0, Om, dU);
+                    // T = Omega Pa + C_U dU
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        double v = 0.0;
+#pragma unroll
+                        for (int e = 0; e < G; ++e) v += CU[c * G + e] * dU[e];
+                        T[c] = v;
+                    }
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int J = 0; J < D; ++J) {
+                            double v = T[i * D + J];
+#pragma unroll
+                            for (int k = 0; k < D; ++k) v += Om[i * D + k] * Pa[k * D + J];
+                            T[i * D + J] = v;
+                        }
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int J = 0; J < D; ++J) {
+                            double v = 0.0;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) v += R[i * D + k] * T[k * D + J];
+                            a.dPdF[((int64_t)gp * G + i * D + J) * G + i0 * D + J0] = v;
+                        }
+                }
+#pragma unroll
+            for (int v = 0; v < NS; ++v) {
+                int i1, j1;
+                voigt_pair(D, v, i1, j1);
+                a.Uprev[(int64_t)gp * NS + v] = U[i1 * D + j1];
+            }
+        }
+    } else if (lane == 0) {
+        a.status[gp] = flag;
+        a.rnorm[gp] = __longlong_as_double(0x7ff8000000000000ll);
+        for (int c = 0; c < G; ++c) a.Pbar[(int64_t)gp * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+        for (int c = 0; c < G * G; ++c) a.dPdF[(int64_t)gp * G * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+// ---- mixed form: per-point phases on the float32 pipe -----------------------
+// y / d to double-float accuracy for a float divisor d with reciprocal inv:
+// q1 = y.hi inv, remainder y - q1 d (exact product), q2 = remainder inv.
+__device__ __forceinline__ df df_div_f(df y, float d, float inv) {
+    const float q1 = __fmul_rn(y.hi, inv);
+    const df r = df_sub(y, df_mul_f(df{q1, 0.0f}, d));
+    return fast_two_sum(q1, __fmul_rn(r.hi, inv));
+}
+
+// Static condensation of one point by one warp, mixed form: the K block of
+// M is factored in float32, the right-hand side [r; V0 Pbar_U] is carried in
+// double-float (yh, yl), X = K^-1 K_qF in float32.  Same algorithm and
+// outputs as condense_warp.
+template <int D, int NA, int NQ>
+__device__ int condense_warp_mix(float *M, float *yh, float *yl, float *X, const float *rh, const float *rl,
+                                 const float *puh, const float *pul, int n, int lane) {
+    constexpr int G = D * D;
+    const int na = n + G;
+    for (int i = lane; i < na; i += 32) {
+        yh[i] = (i < n) ? rh[i] : puh[i - n];
+        yl[i] = (i < n) ? rl[i] : pul[i - n];
+    }
+    bool fin = true;
+    for (int i = lane; i < n; i += 32) fin = fin && isfinite(rh[i]) && isfinite(rl[i]);
+    fin = __all_sync(0xffffffffu, fin);
+    if (!fin) return ST_NONFINITE;
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const float piv = M[k * NA + k];
+        if (!(piv > 0.0f) || !isfinite(piv)) return ST_NONSPD;
+        const float lkk = sqrtf(piv);
+        const float inv = 1.0f / lkk;
+        const df yk = df_div_f(df{yh[k], yl[k]}, lkk, inv);
+        __syncwarp();
+        for (int i = k + 1 + lane; i < na; i += 32) {
+            const float lik = M[i * NA + k] * inv;
+            M[i * NA + k] = lik;
+            const df v = df_sub(df{yh[i], yl[i]}, df_mul_f(yk, lik));
+            yh[i] = v.hi;
+            yl[i] = v.lo;
+        }
+        if (lane == 0) {
+            M[k * NA + k] = lkk;
+            yh[k] = yk.hi;
+            yl[k] = yk.lo;
+        }
+        __syncwarp();
+        for (int i = k + 1; i < na; ++i) {
+            const float lik = M[i * NA + k];
+            for (int j = k + 1 + lane; j <= i; j += 32) M[i * NA + j] -= lik * M[j * NA + k];
+        }
+        __syncwarp();
+    }
+    for (int x = lane; x < G * n; x += 32) {
+        const int c = x / n, j = x % n;
+        X[c * NQ + j] = M[(n + c) * NA + j];
+    }
+    __syncwarp();
+    for (int k = n - 1; k >= 0; --k) {
+        const float lkk = M[k * NA + k];
+        const float inv = 1.0f / lkk;
+        const df sk = df_div_f(df{yh[k], yl[k]}, lkk, inv);
+        float xk[G];
+#pragma unroll
+        for (int c = 0; c < G; ++c) xk[c] = X[c * NQ + k] * inv;
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) {
+            const float lki = M[k * NA + i];
+            const df v = df_sub(df{yh[i], yl[i]}, df_mul_f(sk, lki));
+            yh[i] = v.hi;
+            yl[i] = v.lo;
+#pragma unroll
+            for (int c = 0; c < G; ++c) X[c * NQ + i] -= lki * xk[c];
+        }
+        if (lane == 0) {
+            yh[k] = sk.hi;
+            yl[k] = sk.lo;
+#pragma unroll
+            for (int c = 0; c < G; ++c) X[c * NQ + k] = xk[c];
+        }
+        __syncwarp();
+    }
+    return ST_OK;
+}
+
+// float32 polar-derivative direction (same formulas as polar_dir)
+template <int D>
+__device__ void polar_dir_f(const float *R, const float *U, int i0, int J0, float *Om, float *dU) {
+    constexpr int G = D * D;
+    float X[G], W[G];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) X[a * D + b] = (b == J0) ? R[i0 * D + a] : 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) W[a * D + b] = X[a * D + b] - X[b * D + a];
+    if (D == 2) {
+        const float om = W[2] / (U[0] + U[3]);
+        Om[0] = 0.0f;
+        Om[1] = -om;
+        Om[2] = om;
+        Om[3] = 0.0f;
+    } else {
+        const float w0 = W[7], w1 = W[2], w2 = W[3];
+        const float tr = U[0] + U[4] + U[8];
+        float Mx[9], Mi[9];
+#pragma unroll
+        for (int x = 0; x < 9; ++x) Mx[x] = -U[x];
+        Mx[0] += tr;
+        Mx[4] += tr;
+        Mx[8] += tr;
+        const float dt = Mx[0] * (Mx[4] * Mx[8] - Mx[5] * Mx[7]) - Mx[1] * (Mx[3] * Mx[8] - Mx[5] * Mx[6]) +
+                         Mx[2] * (Mx[3] * Mx[7] - Mx[4] * Mx[6]);
+        const float r = 1.0f / dt;
+        Mi[0] = (Mx[4] * Mx[8] - Mx[5] * Mx[7]) * r;
+        Mi[1] = (Mx[2] * Mx[7] - Mx[1] * Mx[8]) * r;
+        Mi[2] = (Mx[1] * Mx[5] - Mx[2] * Mx[4]) * r;
+        Mi[3] = (Mx[5] * Mx[6] - Mx[3] * Mx[8]) * r;
+        Mi[4] = (Mx[0] * Mx[8] - Mx[2] * Mx[6]) * r;
+        Mi[5] = (Mx[2] * Mx[3] - Mx[0] * Mx[5]) * r;
+        Mi[6] = (Mx[3] * Mx[7] - Mx[4] * Mx[6]) * r;
+        Mi[7] = (Mx[1] * Mx[6] - Mx[0] * Mx[7]) * r;
+        Mi[8] = (Mx[0] * Mx[4] - Mx[1] * Mx[3]) * r;
+        const float o0 = Mi[0] * w0 + Mi[1] * w1 + Mi[2] * w2;
+        const float o1 = Mi[3] * w0 + Mi[4] * w1 + Mi[5] * w2;
+        const float o2 = Mi[6] * w0 + Mi[7] * w1 + Mi[8] * w2;
+        Om[0] = 0.0f;
+        Om[1] = -o2;
+        Om[2] = o1;
+        Om[3] = o2;
+        Om[4] = 0.0f;
+        Om[5] = -o0;
+        Om[6] = -o1;
+        Om[7] = o0;
+        Om[8] = 0.0f;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            float v = X[a * D + b];
+#pragma unroll
+            for (int k = 0; k < D; ++k) v -= Om[a * D + k] * U[k * D + b];
+            dU[a * D + b] = v;
+        }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a + 1; b < D; ++b) {
+            const float v = 0.5f * (dU[a * D + b] + dU[b * D + a]);
+            dU[a * D + b] = v;
+            dU[b * D + a] = v;
+        }
+}
+
+// Outputs of one point by one warp, mixed form: state and rnorm by all
+// lanes, Pbar = R Pbar_alg in double-float (lane 0), tangent column e by
+// lane e in float32 (the tangent is a float32 quantity of this form).
+template <int D, int NA, int NQ>
+__device__ void write_outputs_warp_mix(const EvalArgs &a, int gp, int flag, int n, const float *yh,
+                                       const float *yl, const float *X, const float *M, const double *qd,
+                                       const float *rh, const double *Rm, const double *Um, float V0inv,
+                                       int lane) {
+    constexpr int G = D * D, NS = Dims<D>::NS;
+    if (flag != ST_OK) {
+        if (lane == 0) {
+            a.status[gp] = flag;
+            a.rnorm[gp] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        for (int c = lane; c < G + G * G; c += 32) {
+            if (c < G) a.Pbar[(int64_t)gp * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+            else a.dPdF[(int64_t)gp * G * G + c - G] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        return;
+    }
+    for (int j = lane; j < a.nmax; j += 32) {
+        const int64_t base = (int64_t)gp * a.nmax + j;
+        const bool in = j < n;
+        a.q[base] = in ? qd[j] : 0.0;
+        a.s[base] = in ? df_to(df{yh[j], yl[j]}) : 0.0;
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            int i1, j1;
+            voigt_pair(D, v, i1, j1);
+            float sv = 0.0f;
+            if (in) sv = (i1 == j1) ? X[(i1 * D + j1) * NQ + j] : X[(i1 * D + j1) * NQ + j] + X[(j1 * D + i1) * NQ + j];
+            a.S[base * NS + v] = (double)sv;
+        }
+    }
+    float rmax = 0.0f;
+    for (int j = lane; j < n; j += 32) rmax = fmaxf(rmax, fabsf(rh[j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+    float R[G], U[G], Pa[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+        R[c] = (float)Rm[c];
+        U[c] = (float)Um[c];
+        Pa[c] = yh[n + c] * V0inv;
+    }
+    if (lane == 0) {
+        a.rnorm[gp] = (double)rmax;
+        a.status[gp] = ST_OK;
+        // Pbar = R Pbar_alg with Pbar_alg = y[n:] / V0 in double-float
+        const double iV = 1.0 / a.V0;
+        df Rd[G], Pd[G];
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            Rd[c] = df_from(Rm[c]);
+            Pd[c] = df{yh[n + c], yl[n + c]};
+        }
+        const df iVd = df_from(iV);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int J = 0; J < D; ++J) {
+                df v{0.0f, 0.0f};
+#pragma unroll
+                for (int k = 0; k < D; ++k) v = df_add(v, df_mul(Rd[i * D + k], Pd[k * D + J]));
+                a.Pbar[(int64_t)gp * G + i * D + J] = df_to(df_mul(v, iVd));
+#pragma unroll
+                for (int v2 = 0; v2 < NS; ++v2) {
+                    int i1, j1;
+                    voigt_pair(D, v2, i1, j1);
+                    if (i == 0 && J == 0) a.Uprev[(int64_t)gp * NS + v2] = Um[i1 * D + j1];
+                }
+            }
+    }
+    if (lane < G) {
+        const int i0 = lane / D, J0 = lane % D;
+        float Om[G], dU[G], T[G];
+        polar_dir_f<D>(R, U, i0, J0, Om, dU);
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            float v = 0.0f;
+#pragma unroll
+            for (int e = 0; e < G; ++e) {
+                const int hi = c > e ? c : e, lo = c > e ? e : c;
+                v += M[(n + hi) * NA + n + lo] * V0inv * dU[e];
+            }
+            T[c] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int J = 0; J < D; ++J) {
+                float v = T[i * D + J];
+#pragma unroll
+                for (int k = 0; k < D; ++k) v += Om[i * D + k] * Pa[k * D + J];
+                T[i * D + J] = v;
+            }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int J = 0; J < D; ++J) {
+                float v = 0.0f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) v += R[i * D + k] * T[k * D + J];
+                a.dPdF[((int64_t)gp * G + i * D + J) * G + lane] = (double)v;
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // shared-memory plan of the evaluation kernel (MIX: float32 contraction with
 // double-float kinematics/law/residual; otherwise everything float64)
@@ -708,6 +1158,10 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
         }
 
         // ---- spill accumulators for the condensation ----------------------
+        // (MIX keeps r and V0 Pbar_U as double-float pairs: hi in the first,
+        // lo in the second half of the float view of s_r / s_PU)
+        float *s_rh = reinterpret_cast<float *>(s_r), *s_rl = s_rh + NP * NQ;
+        float *s_puh = reinterpret_cast<float *>(s_PU), *s_pul = s_puh + NP * G;
 #pragma unroll
         for (int x = 0; x < TA; ++x)
 #pragma unroll
@@ -716,84 +1170,40 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int o = tid + u * NT;
-            if (o < NP * NQ) s_r[o] = MIX ? df_to(dacc_get(rdacc[u])) : racc[u];
+            if (o < NP * NQ) {
+                if (MIX) {
+                    const df v = dacc_get(rdacc[u]);
+                    s_rh[o] = v.hi;
+                    s_rl[o] = v.lo;
+                } else {
+                    s_r[o] = racc[u];
+                }
+            }
         }
-        if (tid < NP * G) s_PU[tid] = MIX ? df_to(pudf) : pu;
+        if (tid < NP * G) {
+            if (MIX) {
+                s_puh[tid] = pudf.hi;
+                s_pul[tid] = pudf.lo;
+            } else {
+                s_PU[tid] = pu;
+            }
+        }
         __syncthreads();
         // ---- a6: condensation, one warp per point --------------------------
         const int warp = tid >> 5, lane = tid & 31;
         for (int p = warp; p < NP; p += NT / 32) {
             if (s_flag[p] != ST_OK) continue;
-            KT *M = s_M + p * NA * NA;
-            double *y = s_y + p * NA;
-            for (int i = lane; i < na; i += 32) y[i] = (i < n) ? s_r[p * NQ + i] : s_PU[p * G + i - n];
-            bool fin = true;
-            for (int i = lane; i < n; i += 32) fin = fin && isfinite(s_r[p * NQ + i]);
-            fin = __all_sync(0xffffffffu, fin);
-            if (!fin) {
-                if (lane == 0) s_flag[p] = ST_NONFINITE;
-                continue;
+            int st;
+            if (MIX) {
+                float *yh = reinterpret_cast<float *>(s_y + p * NA);
+                st = condense_warp_mix<D, NA, NQ>(reinterpret_cast<float *>(s_M + p * NA * NA), yh, yh + NA,
+                                                  reinterpret_cast<float *>(s_X + p * G * NQ), s_rh + p * NQ,
+                                                  s_rl + p * NQ, s_puh + p * G, s_pul + p * G, n, lane);
+            } else {
+                st = condense_warp<D, NA, NQ, KT, XT>(s_M + p * NA * NA, s_y + p * NA, s_X + p * G * NQ,
+                                                    s_r + p * NQ, s_PU + p * G, n, lane);
             }
-            __syncwarp();
-            bool spd = true;
-            for (int k = 0; k < n; ++k) {
-                const KT piv = M[k * NA + k];
-                if (!(piv > (KT)0) || !isfinite((double)piv)) {
-                    spd = false;
-                    break;
-                }
-                const KT lkk = sqrt(piv);
-                const KT inv = (KT)1 / lkk;
-                const double yk = y[k] / (double)lkk;
-                __syncwarp();
-                for (int i = k + 1 + lane; i < na; i += 32) {
-                    const KT lik = M[i * NA + k] * inv;
-                    M[i * NA + k] = lik;
-                    y[i] -= (double)lik * yk;
-                }
-                if (lane == 0) {
-                    M[k * NA + k] = lkk;
-                    y[k] = yk;
-                }
-                __syncwarp();
-                for (int i = k + 1; i < na; ++i) {
-                    const KT lik = M[i * NA + k];
-                    for (int j = k + 1 + lane; j <= i; j += 32) M[i * NA + j] -= lik * M[j * NA + k];
-                }
-                __syncwarp();
-            }
-            if (!spd) {
-                if (lane == 0) s_flag[p] = ST_NONSPD;
-                continue;
-            }
-            // s = L^-T y[0:n)  and  X = L^-T Z^T,  Z = rows n.. of the factor
-            XT *X = s_X + p * G * NQ;
-            for (int x = lane; x < G * n; x += 32) {
-                const int c = x / n, j = x % n;
-                X[c * NQ + j] = (XT)M[(n + c) * NA + j];
-            }
-            __syncwarp();
-            for (int k = n - 1; k >= 0; --k) {
-                const double lkk = (double)M[k * NA + k];
-                const double sk = y[k] / lkk;
-                XT xk[G];
-                const XT lkx = (XT)M[k * NA + k];
-#pragma unroll
-                for (int c = 0; c < G; ++c) xk[c] = X[c * NQ + k] / lkx;
-                __syncwarp();
-                for (int i = lane; i < k; i += 32) {
-                    const KT lki = M[k * NA + i];
-                    y[i] -= (double)lki * sk;
-#pragma unroll
-                    for (int c = 0; c < G; ++c) X[c * NQ + i] -= (XT)lki * xk[c];
-                }
-                if (lane == 0) {
-                    y[k] = sk;
-#pragma unroll
-                    for (int c = 0; c < G; ++c) X[c * NQ + k] = xk[c];
-                }
-                __syncwarp();
-            }
+            if (lane == 0 && st != ST_OK) s_flag[p] = st;
         }
         __syncthreads();
 
@@ -801,104 +1211,21 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
         for (int p = warp; p < NP && !ADJ; p += NT / 32) {
             const int gp = s_pidx[p];
             if (gp < 0) continue;
-            const int flag = s_flag[p];
-            const double *y = s_y + p * NA;
-            const XT *X = s_X + p * G * NQ;
-            const KT *M = s_M + p * NA * NA;
-            if (flag == ST_OK) {
-                for (int j = lane; j < a.nmax; j += 32) {
-                    const int64_t base = (int64_t)gp * a.nmax + j;
-                    const bool in = j < n;
-                    a.q[base] = in ? s_qd[p * QP + j] : 0.0;
-                    a.s[base] = in ? y[j] : 0.0;
-#pragma unroll
-                    for (int v = 0; v < NS; ++v) {
-                        int i1, j1;
-                        voigt_pair(D, v, i1, j1);
-                        double sv = 0.0;
-                        if (in) sv = (i1 == j1) ? (double)X[(i1 * D + j1) * NQ + j]
-                                                : (double)X[(i1 * D + j1) * NQ + j] + (double)X[(j1 * D + i1) * NQ + j];
-                        a.S[base * NS + v] = sv;
-                    }
-                }
-                double rmax = 0.0;
-                for (int j = lane; j < n; j += 32) rmax = fmax(rmax, fabs(s_r[p * NQ + j]));
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
-                if (lane == 0) {
-                    a.rnorm[gp] = rmax;
-                    a.status[gp] = ST_OK;
-                    const double iV = 1.0 / a.V0;
-                    double Pa[G], R[G], U[G], CU[G * G];
-#pragma unroll
-                    for (int c = 0; c < G; ++c) {
-                        Pa[c] = y[n + c] * iV;
-                        R[c] = s_R[p * G + c];
-                        U[c] = s_U[p * G + c];
-                    }
-#pragma unroll
-                    for (int c = 0; c < G; ++c)
-#pragma unroll
-                        for (int e = 0; e < G; ++e) {
-                            const int hi = c > e ? c : e, lo = c > e ? e : c;
-                            CU[c * G + e] = (double)M[(n + hi) * NA + n + lo] * iV;
-                        }
-#pragma unroll
-                    for (int i = 0; i < D; ++i)
-#pragma unroll
-                        for (int J = 0; J < D; ++J) {
-                            double v = 0.0;
-#pragma unroll
-                            for (int k = 0; k < D; ++k) v += R[i * D + k] * Pa[k * D + J];
-                            a.Pbar[(int64_t)gp * G + i * D + J] = v;
-                        }
-#pragma unroll
-                    for (int i0 = 0; i0 < D; ++i0)
-#pragma unroll
-                        for (int J0 = 0; J0 < D; ++J0) {
-                            double Om[G], dU[G], T[G];
-                            polar_dir<D>(R, U, i0, J0, Om, dU);
-                            // T = Omega Pa + C_U dU
-#pragma unroll
-                            for (int c = 0; c < G; ++c) {
-                                double v = 0.0;
-#pragma unroll
-                                for (int e = 0; e < G; ++e) v += CU[c * G + e] * dU[e];
-                                T[c] = v;
-                            }
-#pragma unroll
-                            for (int i = 0; i < D; ++i)
-#pragma unroll
-                                for (int J = 0; J < D; ++J) {
-                                    double v = T[i * D + J];
-#pragma unroll
-                                    for (int k = 0; k < D; ++k) v += Om[i * D + k] * Pa[k * D + J];
-                                    T[i * D + J] = v;
-                                }
-#pragma unroll
-                            for (int i = 0; i < D; ++i)
-#pragma unroll
-                                for (int J = 0; J < D; ++J) {
-                                    double v = 0.0;
-#pragma unroll
-                                    for (int k = 0; k < D; ++k) v += R[i * D + k] * T[k * D + J];
-                                    a.dPdF[((int64_t)gp * G + i * D + J) * G + i0 * D + J0] = v;
-                                }
-                        }
-#pragma unroll
-                    for (int v = 0; v < NS; ++v) {
-                        int i1, j1;
-                        voigt_pair(D, v, i1, j1);
-                        a.Uprev[(int64_t)gp * NS + v] = U[i1 * D + j1];
-                    }
-                }
-            } else if (lane == 0) {
-                a.status[gp] = flag;
-                a.rnorm[gp] = __longlong_as_double(0x7ff8000000000000ll);
-                for (int c = 0; c < G; ++c) a.Pbar[(int64_t)gp * G + c] = __longlong_as_double(0x7ff8000000000000ll);
-                for (int c = 0; c < G * G; ++c) a.dPdF[(int64_t)gp * G * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+            if (MIX) {
+                const float *yh = reinterpret_cast<const float *>(s_y + p * NA);
+                write_outputs_warp_mix<D, NA, NQ>(a, gp, s_flag[p], n, yh, yh + NA,
+                                                  reinterpret_cast<const float *>(s_X + p * G * NQ),
+                                                  reinterpret_cast<const float *>(s_M + p * NA * NA),
+                                                  s_qd + p * QP, s_rh + p * NQ, s_R + p * G, s_U + p * G,
+                                                  (float)(1.0 / a.V0), lane);
+            } else {
+                write_outputs_warp<D, NA, NQ, KT, XT>(a, gp, s_flag[p], n, s_y + p * NA, s_X + p * G * NQ,
+                                                    s_M + p * NA * NA, s_qd + p * QP, s_r + p * NQ, s_R + p * G,
+                                                    s_U + p * G, lane);
             }
         }
+        __syncthreads();
+
         if (ADJ) {
             // cotangent on Fbar through the condensed tangent, and z = K^-1 K_qF R^T gP
             for (int p = warp; p < NP; p += NT / 32) {

@@ -51,6 +51,42 @@ __global__ void bucket_scatter(const int32_t *type, int64_t n, int n_types, int3
 
 bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) || (dim == 3 && n <= 47)); }
 
+#define RV_FUSED(D, NA, TA, TB, NP, CI, KT) &launch_cfg<D, NA, TA, TB, NP, CI, KT, false>
+#define RV_WS(D, NA, TA, TB, NP, CI) &launch_ws<D, NA, TA, TB, NP, CI>
+
+int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out) {
+    LaunchFn c[4] = {};
+    int k = 0;
+    if (dim == 2 && mixed) {
+        if (n <= 12) {
+            c[k++] = RV_FUSED(2, 16, 4, 4, 16, 16, float);
+            c[k++] = RV_WS(2, 16, 4, 4, 8, 16);
+        } else if (n <= 16) {
+            c[k++] = RV_FUSED(2, 20, 5, 5, 16, 8, float);
+            c[k++] = RV_WS(2, 20, 5, 5, 8, 16);
+            c[k++] = RV_FUSED(2, 20, 5, 5, 16, 16, float);
+        } else if (n <= 24) {
+            c[k++] = RV_FUSED(2, 28, 7, 7, 16, 16, float);
+            c[k++] = RV_WS(2, 28, 7, 7, 8, 16);
+            c[k++] = RV_FUSED(2, 28, 7, 7, 16, 8, float);
+        } else if (n <= 32) {
+            c[k++] = RV_FUSED(2, 36, 9, 9, 16, 8, float);
+        } else if (n <= 64) {
+            c[k++] = RV_FUSED(2, 72, 9, 9, 4, 8, float);
+        }
+    } else if (dim == 2) {
+        if (n <= 12) c[k++] = RV_FUSED(2, 16, 4, 4, 16, 8, double);
+        else if (n <= 16) c[k++] = RV_FUSED(2, 20, 5, 5, 16, 8, double);
+        else if (n <= 24) c[k++] = RV_FUSED(2, 28, 7, 7, 8, 8, double);
+        else if (n <= 32) c[k++] = RV_FUSED(2, 36, 9, 9, 8, 8, double);
+        else if (n <= 64) c[k++] = RV_FUSED(2, 72, 9, 9, 2, 8, double);
+    } else if (dim == 3) {
+        if (n <= 47) c[k++] = mixed ? RV_FUSED(3, 56, 7, 7, 4, 8, float) : RV_FUSED(3, 56, 7, 7, 2, 4, double);
+    }
+    for (int i = 0; i < k && i < max_out; ++i) out[i] = c[i];
+    return k < max_out ? k : max_out;
+}
+
 }  // namespace rverom
 
 // ---------------------------------------------------------------------------
@@ -235,11 +271,126 @@ extern "C" int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *t
             a.count = nullptr;
             a.offset = nullptr;
         }
+        LaunchFn cand[8];
+        const int nc = forward_candidates(h->dim, a.t.n, precision == RVEROM_MIXED, cand, 8);
+        const int pick = h->choice[t][precision == RVEROM_MIXED ? 1 : 0];
+        if (nc < 1) return RVEROM_ERR_UNSUPPORTED;
         int grid = 0;
-        cudaError_t e = dispatch_eval<false>(h->dim, a.t.n, precision == RVEROM_MIXED, a, h->n_sm, n_points, st, &grid);
+        cudaError_t e = cand[(pick >= 0 && pick < nc) ? pick : 0](a, h->n_sm, n_points, st, &grid);
         if (e != cudaSuccess) return RVEROM_ERR_CUDA;
     }
     return RVEROM_OK;
 }
 
-template cudaError_t rverom::dispatch_eval<false>(int, int, bool, const EvalArgs &, int, int64_t, cudaStream_t, int *);
+// ---------------------------------------------------------------------------
+// autotuner: time every candidate configuration of every type on a sample
+// batch (fresh states at seeded stretches, in device memory allocated here)
+// and keep the fastest per type for this precision.
+namespace {
+__global__ void k_tune_inputs(int64_t n, int dim, int nmax, double *Fbar, double *q, double *s, double *S,
+                              double *Uprev) {
+    const int g = dim * dim, ns = dim == 2 ? 3 : 6;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        // deterministic small stretches: U = I + e (symmetric), |e| <= 0.05
+        unsigned h = (unsigned)(i * 2654435761u) ^ 0x9e3779b9u;
+        for (int c = 0; c < g; ++c) Fbar[i * g + c] = (c % (dim + 1) == 0) ? 1.0 : 0.0;
+        for (int a = 0; a < dim; ++a)
+            for (int b = a; b < dim; ++b) {
+                h = h * 1664525u + 1013904223u;
+                const double v = 0.05 * ((double)(h >> 8) / 16777216.0 - 0.5);
+                Fbar[i * g + a * dim + b] += v;
+                if (a != b) Fbar[i * g + b * dim + a] += v;
+            }
+        for (int j = 0; j < nmax; ++j) {
+            q[i * nmax + j] = 0.0;
+            s[i * nmax + j] = 0.0;
+            for (int v = 0; v < ns; ++v) S[(i * nmax + j) * ns + v] = 0.0;
+        }
+        for (int v = 0; v < ns; ++v) Uprev[i * ns + v] = v < dim ? 1.0 : 0.0;
+    }
+}
+}  // namespace
+
+extern "C" int rve_rom_select_kernel(rverom_t h, int32_t type, int32_t precision, int32_t candidate,
+                                     int32_t *n_candidates) {
+    if (!h || type < 0 || type >= h->n_types || (precision != RVEROM_FP64 && precision != RVEROM_MIXED))
+        return RVEROM_ERR_ARG;
+    LaunchFn cand[8];
+    const int nc = forward_candidates(h->dim, h->types[type].n, precision == RVEROM_MIXED, cand, 8);
+    if (n_candidates) *n_candidates = nc;
+    if (candidate < 0) return RVEROM_OK;  // query only
+    if (candidate >= nc) return RVEROM_ERR_ARG;
+    h->choice[type][precision == RVEROM_MIXED ? 1 : 0] = candidate;
+    return RVEROM_OK;
+}
+
+extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample, float *ms_out, void *stream) {
+    if (!h || (precision != RVEROM_FP64 && precision != RVEROM_MIXED) || n_sample < 1 || n_sample > (1 << 22))
+        return RVEROM_ERR_ARG;
+    const int g = h->dim * h->dim, ns = h->dim == 2 ? 3 : 6;
+    const int64_t n = n_sample;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *buf = nullptr;
+    int32_t *status = nullptr;
+    const size_t nd = (size_t)n * (g + 2 * h->nmax + h->nmax * ns + ns + g + g * g + 1);
+    if (cudaMalloc(&buf, nd * sizeof(double)) != cudaSuccess) return RVEROM_ERR_CUDA;
+    if (cudaMalloc(&status, (size_t)n * sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(buf);
+        return RVEROM_ERR_CUDA;
+    }
+    double *Fbar = buf, *q = Fbar + n * g, *s = q + n * h->nmax, *S = s + n * h->nmax, *U = S + n * h->nmax * ns;
+    double *Pbar = U + n * ns, *dPdF = Pbar + n * g, *rnorm = dPdF + n * g * g;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = RVEROM_OK;
+    const int pi = precision == RVEROM_MIXED ? 1 : 0;
+    for (int t = 0; t < h->n_types && rc == RVEROM_OK; ++t) {
+        LaunchFn cand[8];
+        const int nc = forward_candidates(h->dim, h->types[t].n, precision == RVEROM_MIXED, cand, 8);
+        float best = 1e30f;
+        int bi = 0;
+        for (int c = 0; c < nc; ++c) {
+            EvalArgs a = {};
+            a.t = h->types[t];
+            a.n_points = n;
+            a.nmax = h->nmax;
+            a.V0 = h->V0;
+            a.Fbar = Fbar;
+            a.q = q;
+            a.s = s;
+            a.S = S;
+            a.Uprev = U;
+            a.Pbar = Pbar;
+            a.dPdF = dPdF;
+            a.rnorm = rnorm;
+            a.status = status;
+            float tbest = 1e30f;
+            for (int rep = 0; rep < 3 && rc == RVEROM_OK; ++rep) {
+                k_tune_inputs<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(
+                    n, h->dim, h->nmax, Fbar, q, s, S, U);
+                int grid = 0;
+                cudaEventRecord(e0, st);
+                if (cand[c](a, h->n_sm, n, st, &grid) != cudaSuccess) rc = RVEROM_ERR_CUDA;
+                cudaEventRecord(e1, st);
+                float ms = 0.0f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                    rc = RVEROM_ERR_CUDA;
+                if (rep > 0 && ms < tbest) tbest = ms;  // first repetition warms up
+            }
+            if (ms_out) ms_out[t * RVEROM_MAX_CANDIDATES + c] = tbest;
+            if (tbest < best) {
+                best = tbest;
+                bi = c;
+            }
+        }
+        for (int c = nc; ms_out && c < RVEROM_MAX_CANDIDATES; ++c) ms_out[t * RVEROM_MAX_CANDIDATES + c] = -1.0f;
+        h->choice[t][pi] = bi;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    cudaFree(status);
+    return rc;
+}

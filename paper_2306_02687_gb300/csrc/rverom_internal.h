@@ -5,6 +5,7 @@
 
 #include "../../include/rverom.h"
 #include "rom_core.cuh"
+#include "rom_ws.cuh"
 
 struct rverom_s {
     int dim = 2;
@@ -19,6 +20,7 @@ struct rverom_s {
     int64_t perm_cap = 0;
     double *partials = nullptr;       // per-CTA partial sums of the adjoint
     int64_t partials_cap = 0;
+    int choice[RVEROM_MAX_TYPES][2] = {};  // forward kernel candidate per type and precision
 };
 
 namespace rverom {
@@ -44,11 +46,36 @@ cudaError_t launch_cfg(const EvalArgs &a, int n_sm, int64_t max_points, cudaStre
     return cudaGetLastError();
 }
 
+// Warp-specialized mixed-precision forward kernel <D, NA, TA, TB, NP, CI>.
+template <int D, int NA, int TA, int TB, int NP, int CI>
+cudaError_t launch_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
+    using PL = WsPlan<D, NA, TA, TB, NP, CI>;
+    auto kern = eval_ws_kernel<D, NA, TA, TB, NP, CI>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PL::NT, PL::bytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int64_t tiles = (max_points + NP - 1) / NP;
+    int64_t grid = (int64_t)n_sm * occ;
+    if (tiles < grid) grid = tiles;
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = (int)grid;
+    kern<<<(unsigned)grid, PL::NT, PL::bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
 // Tile configuration per (dimension, n~ bucket, precision).
 template <bool ADJ>
 cudaError_t dispatch_eval(int dim, int n, bool mixed, const EvalArgs &a, int n_sm, int64_t max_points,
                           cudaStream_t st, int *grid_out) {
     if (dim == 2) {
+        if (mixed && !ADJ) {
+            if (n <= 12) return launch_ws<2, 16, 4, 4, 8, 16>(a, n_sm, max_points, st, grid_out);
+            if (n <= 16) return launch_ws<2, 20, 5, 5, 8, 16>(a, n_sm, max_points, st, grid_out);
+            if (n <= 24) return launch_ws<2, 28, 7, 7, 8, 16>(a, n_sm, max_points, st, grid_out);
+        }
         if (mixed) {
             if (n <= 12) return launch_cfg<2, 16, 4, 4, 16, 16, float, ADJ>(a, n_sm, max_points, st, grid_out);
             if (n <= 16) return launch_cfg<2, 20, 5, 5, 16, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
@@ -74,4 +101,9 @@ cudaError_t dispatch_eval(int dim, int n, bool mixed, const EvalArgs &a, int n_s
 bool supported_modes(int dim, int n);
 int prepare_buckets(rverom_t h, int64_t n, const int32_t *type, int32_t *status, double *rnorm,
                     cudaStream_t st);
+
+// Candidate forward kernels (tile configurations) of an RVE type; entry 0 is
+// the default before autotuning.  Returns the number of candidates.
+using LaunchFn = cudaError_t (*)(const EvalArgs &, int, int64_t, cudaStream_t, int *);
+int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out);
 }  // namespace rverom

@@ -275,3 +275,35 @@ def test_3d_batch():
     for precision, tol in (('fp64', TOL_FP64), ('mixed', TOL_MIXED)):
         g = run_gpu(h, F, q, s, S, U, precision)
         compare(g, oracle_batch(oroms, F, q, s, S, U), h.nmax, tol)
+
+
+@pytest.mark.parametrize('names', [['c1'], ['c2'], ['c5a', 'c5b', 'c5c']])
+def test_every_tile_configuration_matches_oracle(names):
+    # every compiled configuration (and the autotuner's pick) meets the
+    # mixed-form gate on mid-Newton states
+    import os
+    if not all(os.path.exists(rom_path(nm)) for nm in names):
+        pytest.skip('ROM files not generated')
+    h, oroms = _handle(names)
+    n = 21
+    types = syn.type_labels(syn.SEED_BASE + 70, n, len(names)) if len(names) > 1 else None
+    F = np.zeros((n, 2, 2))
+    q = np.zeros((n, h.nmax))
+    s = np.zeros((n, h.nmax))
+    S = np.zeros((n, h.nmax, 3))
+    U = np.zeros((n, 3))
+    for t in range(len(names)):
+        sel = np.arange(n) if types is None else np.nonzero(types == t)[0]
+        Fm, qm, sm, Sm, Um = mid_newton_inputs(oroms[t], len(sel), syn.SEED_BASE + 71 + t)
+        k = oroms[t].n
+        F[sel], q[sel, :k], s[sel, :k], S[sel, :k], U[sel] = Fm, qm, sm, Sm, Um
+    outs = oracle_batch(oroms, F, q, s, S, U, types)
+    for precision, tol in (('fp64', TOL_FP64), ('mixed', TOL_MIXED)):
+        counts = [rv.rve_rom_select_kernel(h, t, precision) for t in range(len(names))]
+        for c in range(max(counts)):
+            for t in range(len(names)):
+                rv.rve_rom_select_kernel(h, t, precision, min(c, counts[t] - 1))
+            compare(run_gpu(h, F, q, s, S, U, precision, types=types), outs, h.nmax, tol)
+        ms = rv.rve_rom_autotune(h, precision, n_sample=2048)
+        assert np.all(ms[:, 0] > 0)
+        compare(run_gpu(h, F, q, s, S, U, precision, types=types), outs, h.nmax, tol)
