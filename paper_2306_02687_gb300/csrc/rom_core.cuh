@@ -61,9 +61,20 @@ struct TypeDev {
     const float *Bh;   // [m][g][n] float32 leading part of B
     const float *Bl;   // [m][g][n] float32 remainder B - Bh
     const double *w;   // [m]
+    const float *wh;   // [m] float32 leading part of w
+    const float *wl;   // [m] float32 remainder w - wh
     const int *phase;  // [m]
     double mu[2], kappa[2];
 };
+
+// 4-byte asynchronous global -> shared copy (no register round trip)
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 struct EvalArgs {
     TypeDev t;
@@ -764,6 +775,213 @@ __device__ void write_outputs_warp_mix(const EvalArgs &a, int gp, int flag, int 
     }
 }
 
+// Register-resident condensation and outputs of one point by one warp, mixed
+// form, for augmented size NA <= 32.  Lane j holds column j of the symmetric
+// augmented matrix M (rows in registers col[0..NA)); every pivot step keeps
+// the trailing block symmetric (full-square update), so the L entry a lane
+// needs is its own row-k element and the row entries of the other lanes come
+// by warp shuffles.  The right-hand side [r; V0 Pbar_U] is double-float, the
+// coupling solve X = K^-1 K_qF float32.  Writes the same outputs as
+// condense_warp_mix followed by write_outputs_warp_mix; returns the status.
+template <int NA>
+__device__ __forceinline__ float sel(const float (&col)[NA], int k) {
+    // element k (warp-uniform, 0 <= k < NA) by a select tree on the bits of k
+    float t[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) t[i] = i < NA ? col[i] : 0.0f;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool hi = (k & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) t[i] = hi ? t[i + w] : t[i];
+    }
+    return t[0];
+}
+
+__device__ __forceinline__ df shfl_df(df v, int src) {
+    return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = df_add(v, df{__shfl_xor_sync(0xffffffffu, v.hi, off),
+                                                           __shfl_xor_sync(0xffffffffu, v.lo, off)});
+    return v;
+}
+
+template <int D, int NA, int NQ>
+__device__ int condense_out_regs_mix(const EvalArgs &a, const float *Msm, const float *rh, const float *rl,
+                                     const float *puh, const float *pul, int gp, int flag, int n,
+                                     const double *qd, const double *Rm, const double *Um, float V0inv,
+                                     int lane) {
+    static_assert(NA <= 32, "one column per lane");
+    constexpr int G = D * D, NS = Dims<D>::NS;
+    const int na = n + G;
+    const int j = lane;
+    const bool colj = j < na;
+    float col[NA], Lc[NA];  // column j of M / of the factor L (lane j = pivot k keeps L[:, k])
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+        col[i] = (colj && i < na) ? Msm[i * NA + j] : 0.0f;
+        Lc[i] = 0.0f;
+    }
+    df y{0.0f, 0.0f};
+    if (j < n) y = df{rh[j], rl[j]};
+    else if (colj) y = df{puh[j - n], pul[j - n]};
+    const float rj = (j < n) ? rh[j] : 0.0f;
+    bool fin = (j < n) ? (isfinite(rh[j]) && isfinite(rl[j])) : true;
+    int st = flag;
+    if (st == ST_OK && !__all_sync(0xffffffffu, fin)) st = ST_NONFINITE;
+    // ---- forward: Cholesky of the K block carried through coupling and rhs
+    for (int k = 0; k < n && st == ST_OK; ++k) {
+        const float rowk = sel(col, k);                      // M[k][j] (= M[j][k])
+        const float d = __shfl_sync(0xffffffffu, rowk, k);
+        if (!(d > 0.0f) || !isfinite(d)) {
+            st = ST_NONSPD;
+            break;
+        }
+        const float lkk = sqrtf(d), inv = 1.0f / lkk;
+        const float l = (j > k && colj) ? rowk * inv : 0.0f;  // L[j][k]
+        const df yk = df_div_f(shfl_df(y, k), lkk, inv);
+        if (j > k && colj) y = df_sub(y, df_mul_f(yk, l));
+        if (j == k) y = yk;
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const float li = __shfl_sync(0xffffffffu, l, i);
+            col[i] = (i > k) ? __fmaf_rn(-li, l, col[i]) : col[i];
+            Lc[i] = (j == k) ? ((i == k) ? lkk : li) : Lc[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NA; ++i) col[i] = (i == k) ? ((j == k) ? lkk : l) : col[i];
+    }
+    const int gst = __shfl_sync(0xffffffffu, st, 0);
+    if (gst != ST_OK) {
+        if (lane == 0) {
+            a.status[gp] = gst;
+            a.rnorm[gp] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        for (int c = lane; c < G + G * G; c += 32) {
+            if (c < G) a.Pbar[(int64_t)gp * G + c] = __longlong_as_double(0x7ff8000000000000ll);
+            else a.dPdF[(int64_t)gp * G * G + c - G] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        return gst;
+    }
+    // ---- backward, column-oriented: s = L^-T y and X = L^-T Z^T (Z = coupling
+    // rows of L).  Lane i updates its right-hand side with L[k][i] = Lc[k] of
+    // lane i (its own column of L) and the broadcast solution entry k.
+    df sj = y;
+    float xj[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) xj[c] = (j < n) ? sel(Lc, n + c) : 0.0f;  // Z[c][j]
+    for (int k = n - 1; k >= 0; --k) {
+        const float lkk = __shfl_sync(0xffffffffu, sel(Lc, k), k);
+        const float inv = 1.0f / lkk;
+        const df sk = df_div_f(shfl_df(sj, k), lkk, inv);
+        const float lki = (j < k) ? sel(Lc, k) : 0.0f;  // L[k][j]
+        if (j < k) sj = df_sub(sj, df_mul_f(sk, lki));
+        if (j == k) sj = sk;
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            const float xk = __shfl_sync(0xffffffffu, xj[c], k) * inv;
+            if (j < k) xj[c] = __fmaf_rn(-lki, xk, xj[c]);
+            if (j == k) xj[c] = xk;
+        }
+    }
+    // ---- outputs
+    if (j < a.nmax) {
+        const int64_t base = (int64_t)gp * a.nmax + j;
+        const bool in = j < n;
+        a.q[base] = in ? qd[j] : 0.0;
+        a.s[base] = in ? df_to(sj) : 0.0;
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            int i1, j1;
+            voigt_pair(D, v, i1, j1);
+            const float sv = (i1 == j1) ? xj[i1 * D + j1] : xj[i1 * D + j1] + xj[j1 * D + i1];
+            a.S[base * NS + v] = in ? (double)sv : 0.0;
+        }
+    }
+    for (int jj = 32 + lane; jj < a.nmax; jj += 32) {        // state padding beyond one warp
+        const int64_t base = (int64_t)gp * a.nmax + jj;
+        a.q[base] = 0.0;
+        a.s[base] = 0.0;
+        for (int v = 0; v < NS; ++v) a.S[base * NS + v] = 0.0;
+    }
+    float rmax = fabsf(rj);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+    // Pbar_alg (double-float, lanes n..n+G-1) and C_U (trailing columns)
+    df Pd[G];
+    float Pa[G], CU[G * G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+        Pd[c] = shfl_df(y, n + c);
+        Pa[c] = Pd[c].hi * V0inv;
+#pragma unroll
+        for (int e = 0; e < G; ++e) CU[c * G + e] = __shfl_sync(0xffffffffu, sel(col, n + c), n + e) * V0inv;
+    }
+    float R[G], U[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+        R[c] = (float)Rm[c];
+        U[c] = (float)Um[c];
+    }
+    if (lane == 0) {
+        a.rnorm[gp] = (double)rmax;
+        a.status[gp] = ST_OK;
+        df Rd[G];
+#pragma unroll
+        for (int c = 0; c < G; ++c) Rd[c] = df_from(Rm[c]);
+        const df iVd = df_from(1.0 / a.V0);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int J = 0; J < D; ++J) {
+                df v{0.0f, 0.0f};
+#pragma unroll
+                for (int k = 0; k < D; ++k) v = df_add(v, df_mul(Rd[i * D + k], Pd[k * D + J]));
+                a.Pbar[(int64_t)gp * G + i * D + J] = df_to(df_mul(v, iVd));
+            }
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            int i1, j1;
+            voigt_pair(D, v, i1, j1);
+            a.Uprev[(int64_t)gp * NS + v] = Um[i1 * D + j1];
+        }
+    }
+    if (lane < G) {
+        const int i0 = lane / D, J0 = lane % D;
+        float Om[G], dU[G], T[G];
+        polar_dir_f<D>(R, U, i0, J0, Om, dU);
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            float v = 0.0f;
+#pragma unroll
+            for (int e = 0; e < G; ++e) v += CU[c * G + e] * dU[e];
+            T[c] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int J = 0; J < D; ++J) {
+                float v = T[i * D + J];
+#pragma unroll
+                for (int k = 0; k < D; ++k) v += Om[i * D + k] * Pa[k * D + J];
+                T[i * D + J] = v;
+            }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int J = 0; J < D; ++J) {
+                float v = 0.0f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) v += R[i * D + k] * T[k * D + J];
+                a.dPdF[((int64_t)gp * G + i * D + J) * G + lane] = (double)v;
+            }
+    }
+    return ST_OK;
+}
+
 // ---------------------------------------------------------------------------
 // shared-memory plan of the evaluation kernel (MIX: float32 contraction with
 // double-float kinematics/law/residual; otherwise everything float64)
@@ -796,15 +1014,17 @@ struct Plan {
     static constexpr int o_y = o_w + CI;
     static constexpr int o_X = o_y + NP * NA;
     static constexpr int o_q64 = o_X + NP * G * NQ;   // float64 q (MIX keeps split copies in o_q)
-    static constexpr int n_dbl = o_q64 + NP * QP;
+    static constexpr int o_B2 = o_q64 + NP * QP;       // MIX: second staging buffer (Bh | Bl)
+    static constexpr int o_w2 = o_B2 + (MIX ? CI * G * BP : 0);
+    static constexpr int n_dbl = o_w2 + (MIX ? CI : 0);
     // ints
-    static constexpr int o_ph = 0;
-    static constexpr int o_flag = o_ph + CI;
+    static constexpr int o_ph = 0;                    // [2][CI] (MIX double-buffers)
+    static constexpr int o_flag = o_ph + 2 * CI;
     static constexpr int o_pidx = o_flag + NP;
     static constexpr int n_int = ((o_pidx + NP + 3) / 4) * 4;
     // KT arrays
-    static constexpr int o_Bx = 0;
-    static constexpr int o_YM = o_Bx + KC * NA;
+    static constexpr int o_Bx = 0;                    // [MIX ? 2 : 1][KC][NA]
+    static constexpr int o_YM = o_Bx + (MIX ? 2 : 1) * KC * NA;
     static constexpr int NAP = NA + 1;                 // padded Y row (bank conflicts)
     static constexpr int n_YM = (NP * KC * NAP > NP * NA * NA) ? NP * KC * NAP : NP * NA * NA;
     static constexpr int n_kt = o_YM + n_YM;
@@ -864,6 +1084,20 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
         dlam1 = df_from(a.t.kappa[1] - (2.0 / 3.0) * a.t.mu[1]);
     }
 
+    if (MIX) {
+        // staging buffers: zero once (entries past m keep finite values), then
+        // the constant identity block of [B_i | I] in both Bx buffers
+        float *b0 = reinterpret_cast<float *>(s_B), *b1 = reinterpret_cast<float *>(sd + PL::o_B2);
+        for (int x = tid; x < 2 * CI * G * BP; x += NT) {
+            b0[x] = 0.0f;
+            b1[x] = 0.0f;
+        }
+        for (int x = tid; x < 2 * KC * NA; x += NT) {
+            const int k = (x / NA) % KC, col = x % NA, c = k % G;
+            s_Bx[x] = (col >= n && col - n == c) ? (KT)1 : (KT)0;
+        }
+        __syncthreads();
+    }
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         // ---- a1: polar split, micro update --------------------------------
         if (tid < NP) {
@@ -943,51 +1177,77 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
                 kc[x][y] = (KT)0;
             }
         double racc[RPT];
-        dacc rdacc[RPT];
+        dacc rdacc[2 * RPT];  // MIX: two independent chains per output (even / odd il)
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            racc[u] = 0.0;
-            rdacc[u] = dacc{0.0f, 0.0f};
-        }
+        for (int u = 0; u < RPT; ++u) racc[u] = 0.0;
+#pragma unroll
+        for (int u = 0; u < 2 * RPT; ++u) rdacc[u] = dacc{0.0f, 0.0f};
         double pu = 0.0;
         df pudf = df{0.0f, 0.0f};
         __syncthreads();
 
         // ---- ECM loop: a2-a5 ---------------------------------------------
-        for (int i0 = 0; i0 < m; i0 += CI) {
-            // stage the chunk of the gradient table
-            for (int x = tid; x < CI * G * NQ; x += NT) {
-                const int il = x / (G * NQ), rem = x % (G * NQ), c = rem / NQ, j = rem % NQ;
-                const bool in = i0 + il < m && j < n;
-                const int64_t gi = ((int64_t)(i0 + il) * G + c) * n + j;
-                if (MIX) {
-                    s_Bh[(il * G + c) * BP + j] = in ? a.t.Bh[gi] : 0.0f;
-                    s_Bl[(il * G + c) * BP + j] = in ? a.t.Bl[gi] : 0.0f;
+        // MIX: the gradient table of chunk kch+1 is copied asynchronously
+        // into the other buffer while chunk kch is processed.
+        auto issue_stage = [&](int buf, int i0s) {
+            float *bh = reinterpret_cast<float *>(buf ? sd + PL::o_B2 : sd + PL::o_B);
+            float *bl = bh + CI * G * BP;
+            KT *bx = sk + PL::o_Bx + buf * KC * NA;
+            float *wh = reinterpret_cast<float *>(buf ? sd + PL::o_w2 : sd + PL::o_w);
+            float *wl = wh + CI;
+            const int cnt = min(CI, m - i0s) * G * n;
+            for (int x = tid; x < cnt; x += NT) {
+                const int r = x / n, j = x - r * n;  // r = il * G + c
+                const int64_t gi = (int64_t)i0s * G * n + x;
+                cp_async4(bh + r * BP + j, a.t.Bh + gi);
+                cp_async4(bl + r * BP + j, a.t.Bl + gi);
+                cp_async4(bx + r * NA + j, a.t.Bh + gi);
+            }
+            if (tid < min(CI, m - i0s)) {
+                cp_async4(wh + tid, a.t.wh + i0s + tid);
+                cp_async4(wl + tid, a.t.wl + i0s + tid);
+                cp_async4(s_ph + buf * CI + tid, a.t.phase + i0s + tid);
+            }
+            cp_async_commit();
+        };
+        if (MIX) issue_stage(0, 0);
+        for (int i0 = 0, kch = 0; i0 < m; i0 += CI, ++kch) {
+            const int buf = MIX ? (kch & 1) : 0;
+            if (MIX) {
+                if (i0 + CI < m) {
+                    issue_stage(buf ^ 1, i0 + CI);
+                    cp_async_wait<1>();
                 } else {
+                    cp_async_wait<0>();
+                }
+                s_Bh = buf ? reinterpret_cast<float *>(sd + PL::o_B2) : reinterpret_cast<float *>(s_B);
+                s_Bl = s_Bh + CI * G * BP;
+                s_wh = buf ? reinterpret_cast<float *>(sd + PL::o_w2) : reinterpret_cast<float *>(s_w);
+                s_wl = s_wh + CI;
+                s_Bx = sk + PL::o_Bx + buf * KC * NA;
+            } else {
+                // stage the chunk of the gradient table
+                for (int x = tid; x < CI * G * NQ; x += NT) {
+                    const int il = x / (G * NQ), rem = x % (G * NQ), c = rem / NQ, j = rem % NQ;
+                    const bool in = i0 + il < m && j < n;
+                    const int64_t gi = ((int64_t)(i0 + il) * G + c) * n + j;
                     s_B[(il * G + c) * BP + j] = in ? a.t.B[gi] : 0.0;
                 }
-            }
-            for (int x = tid; x < KC * NA; x += NT) {
-                const int k = x / NA, col = x % NA, il = k / G, c = k % G;
-                KT v = (KT)0;
-                if (i0 + il < m) {
-                    const int64_t gi = ((int64_t)(i0 + il) * G + c) * n + col;
-                    if (col < n) v = MIX ? (KT)a.t.Bh[gi] : (KT)a.t.B[gi];
-                    else if (col - n == c) v = (KT)1;
+                for (int x = tid; x < KC * NA; x += NT) {
+                    const int k = x / NA, col = x % NA, il = k / G, c = k % G;
+                    KT v = (KT)0;
+                    if (i0 + il < m) {
+                        const int64_t gi = ((int64_t)(i0 + il) * G + c) * n + col;
+                        if (col < n) v = (KT)a.t.B[gi];
+                        else if (col - n == c) v = (KT)1;
+                    }
+                    s_Bx[x] = v;
                 }
-                s_Bx[x] = v;
-            }
-            if (tid < CI) {
-                const bool ok = i0 + tid < m;
-                const double wv = ok ? a.t.w[i0 + tid] : 0.0;
-                if (MIX) {
-                    const df w2 = df_from(wv);
-                    s_wh[tid] = w2.hi;
-                    s_wl[tid] = w2.lo;
-                } else {
-                    s_w[tid] = wv;
+                if (tid < CI) {
+                    const bool ok = i0 + tid < m;
+                    s_w[tid] = ok ? a.t.w[i0 + tid] : 0.0;
+                    s_ph[tid] = ok ? a.t.phase[i0 + tid] : 0;
                 }
-                s_ph[tid] = ok ? a.t.phase[i0 + tid] : 0;
             }
             __syncthreads();
 
@@ -996,7 +1256,7 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
                 const int p = task % NP, il = task / NP;
                 KT *yrow = s_Y + ((il * G) * NP + p) * NAP;  // row k = il*G + c at yrow + c*NP*NAP
                 bool live = (s_flag[p] == ST_OK) && (i0 + il < m);
-                const int ph = s_ph[il];
+                const int ph = s_ph[buf * CI + il];
                 KT fi[G];
                 KT lnJk = (KT)0;
                 if (live) {
@@ -1121,22 +1381,34 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
                 }
             }
             // float64-accurate reduced residual and homogenized stress
+            if (MIX) {
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                const int o = tid + u * NT;
-                if (o < NP * NQ) {
-                    const int p = o / NQ, j = o % NQ;
-                    if (j < n) {
-                        if (MIX) {
-                            dacc v = rdacc[u];
-                            for (int il = 0; il < CI; ++il)
+                for (int u = 0; u < RPT; ++u) {
+                    const int o = tid + u * NT;
+                    if (o < NP * NQ) {
+                        const int p = o / NQ, j = o % NQ;
+                        if (j < n) {
+                            dacc v0 = rdacc[2 * u], v1 = rdacc[2 * u + 1];
+                            for (int il = 0; il < CI; il += 2)
 #pragma unroll
                                 for (int c = 0; c < G; ++c) {
-                                    const int bi = (il * G + c) * BP + j, wi = (il * G + c) * NP + p;
-                                    dacc_fma(v, s_Bh[bi], s_Bl[bi], s_WPh[wi], s_WPl[wi]);
+                                    const int b0 = (il * G + c) * BP + j, w0 = (il * G + c) * NP + p;
+                                    const int b1 = b0 + G * BP, w1 = w0 + G * NP;
+                                    dacc_fma(v0, s_Bh[b0], s_Bl[b0], s_WPh[w0], s_WPl[w0]);
+                                    dacc_fma(v1, s_Bh[b1], s_Bl[b1], s_WPh[w1], s_WPl[w1]);
                                 }
-                            rdacc[u] = v;
-                        } else {
+                            rdacc[2 * u] = v0;
+                            rdacc[2 * u + 1] = v1;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < RPT; ++u) {
+                    const int o = tid + u * NT;
+                    if (o < NP * NQ) {
+                        const int p = o / NQ, j = o % NQ;
+                        if (j < n) {
                             double v = racc[u];
                             for (int il = 0; il < CI; ++il)
 #pragma unroll
@@ -1167,17 +1439,21 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
 #pragma unroll
             for (int y = 0; y < TB; ++y)
                 s_M[(tp * NA + a0 + x) * NA + b0 + y] = MIX ? (KT)(kh[x][y] - kc[x][y]) : acc[x][y];
+        if (MIX) {
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            const int o = tid + u * NT;
-            if (o < NP * NQ) {
-                if (MIX) {
-                    const df v = dacc_get(rdacc[u]);
+            for (int u = 0; u < RPT; ++u) {
+                const int o = tid + u * NT;
+                if (o < NP * NQ) {
+                    const df v = df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1]));
                     s_rh[o] = v.hi;
                     s_rl[o] = v.lo;
-                } else {
-                    s_r[o] = racc[u];
                 }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                const int o = tid + u * NT;
+                if (o < NP * NQ) s_r[o] = racc[u];
             }
         }
         if (tid < NP * G) {
@@ -1191,7 +1467,18 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
         __syncthreads();
         // ---- a6: condensation, one warp per point --------------------------
         const int warp = tid >> 5, lane = tid & 31;
-        for (int p = warp; p < NP; p += NT / 32) {
+        constexpr bool REGS = MIX && NA <= 32 && !ADJ;
+        if (REGS) {
+            for (int p = warp; p < NP; p += NT / 32) {
+                const int gp = s_pidx[p];
+                if (gp < 0) continue;
+                condense_out_regs_mix<D, (NA <= 32 ? NA : 32), NQ>(
+                    a, reinterpret_cast<const float *>(s_M + p * NA * NA), s_rh + p * NQ, s_rl + p * NQ,
+                    s_puh + p * G, s_pul + p * G, gp, s_flag[p], n, s_qd + p * QP, s_R + p * G, s_U + p * G,
+                    (float)(1.0 / a.V0), lane);
+            }
+        }
+        for (int p = warp; p < NP && !REGS; p += NT / 32) {
             if (s_flag[p] != ST_OK) continue;
             int st;
             if (MIX) {
@@ -1208,7 +1495,7 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
         __syncthreads();
 
         // ---- a7: outputs ---------------------------------------------------
-        for (int p = warp; p < NP && !ADJ; p += NT / 32) {
+        for (int p = warp; p < NP && !ADJ && !REGS; p += NT / 32) {
             const int gp = s_pidx[p];
             if (gp < 0) continue;
             if (MIX) {

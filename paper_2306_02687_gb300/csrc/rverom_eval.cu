@@ -123,7 +123,12 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
         td.m = d.n_ecm;
         size_t nb = (size_t)d.n_ecm * g * d.n_modes;
         double *B = nullptr, *w = nullptr;
-        float *Bh = nullptr, *Bl = nullptr;
+        float *Bh = nullptr, *Bl = nullptr, *wh = nullptr, *wl = nullptr;
+        std::vector<float> whh(d.n_ecm), wll(d.n_ecm);
+        for (int i = 0; i < d.n_ecm; ++i) {
+            whh[i] = (float)d.w[i];
+            wll[i] = (float)(d.w[i] - (double)whh[i]);
+        }
         int *ph = nullptr;
         std::vector<float> hh(nb), ll(nb);
         for (size_t x = 0; x < nb; ++x) {
@@ -133,6 +138,10 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
         bool ok = cudaMalloc(&B, nb * sizeof(double)) == cudaSuccess &&
                   cudaMalloc(&Bh, nb * sizeof(float)) == cudaSuccess &&
                   cudaMalloc(&Bl, nb * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&wh, d.n_ecm * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&wl, d.n_ecm * sizeof(float)) == cudaSuccess &&
+                  cudaMemcpy(wh, whh.data(), d.n_ecm * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(wl, wll.data(), d.n_ecm * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(Bh, hh.data(), nb * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(Bl, ll.data(), nb * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMalloc(&w, d.n_ecm * sizeof(double)) == cudaSuccess &&
@@ -144,6 +153,8 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
         td.Bh = Bh;
         td.Bl = Bl;
         td.w = w;
+        td.wh = wh;
+        td.wl = wl;
         td.phase = ph;
         for (int k = 0; k < 2; ++k) {
             td.mu[k] = d.moduli[k][0];
@@ -153,10 +164,14 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
             cudaFree(B);
             cudaFree(Bh);
             cudaFree(Bl);
+            cudaFree(wh);
+            cudaFree(wl);
             cudaFree(w);
             cudaFree(ph);
             td.Bh = nullptr;
             td.Bl = nullptr;
+            td.wh = nullptr;
+            td.wl = nullptr;
             td.B = nullptr;
             td.w = nullptr;
             td.phase = nullptr;
@@ -180,6 +195,8 @@ extern "C" int rve_rom_destroy(rverom_t h) {
         cudaFree((void *)h->types[t].B);
         cudaFree((void *)h->types[t].Bh);
         cudaFree((void *)h->types[t].Bl);
+        cudaFree((void *)h->types[t].wh);
+        cudaFree((void *)h->types[t].wl);
         cudaFree((void *)h->types[t].w);
         cudaFree((void *)h->types[t].phase);
     }

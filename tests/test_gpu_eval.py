@@ -104,11 +104,13 @@ def mid_newton_inputs(orom, n, seed, eps=0.1, angle=0.3):
     return F1, q, s, S, U
 
 
-# FP64 form: the same float64 arithmetic in another summation order
-TOL_FP64 = dict(Pbar=1e-12, dPdF=1e-11, s=1e-9, S=1e-9, q=1e-12, Uprev=1e-15, rnorm=1e-9)
+# FP64 form: the same float64 arithmetic in another summation order.  Uprev
+# is the polar stretch, computed by Newton iteration on the GPU and by an
+# eigen-decomposition in the oracle (3D): a few units of rounding apart.
+TOL_FP64 = dict(Pbar=1e-12, dPdF=1e-11, s=1e-9, S=1e-9, q=1e-12, Uprev=1e-14, rnorm=1e-9)
 # mixed form on mid-Newton states: FP64 r and Pbar_U; the Newton correction
 # K_qF^T K^-1 r carries the float32 solve error (small near convergence)
-TOL_MIXED = dict(Pbar=1e-8, dPdF=1e-5, q=1e-12, Uprev=1e-15, rnorm=1e-6)
+TOL_MIXED = dict(Pbar=1e-8, dPdF=1e-5, q=1e-12, Uprev=1e-14, rnorm=1e-6)
 
 
 @pytest.mark.parametrize('n', [1, 15, 37])
