@@ -822,7 +822,8 @@ __device__ int condense_out_regs_mix(const EvalArgs &a, const float *Msm, const 
     float col[NA], Lc[NA];  // column j of M / of the factor L (lane j = pivot k keeps L[:, k])
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-        col[i] = (colj && i < na) ? Msm[i * NA + j] : 0.0f;
+        // lower triangle only (the contraction may skip upper blocks)
+        col[i] = (colj && i < na) ? Msm[(i >= j ? i * NA + j : j * NA + i)] : 0.0f;
         Lc[i] = 0.0f;
     }
     df y{0.0f, 0.0f};
@@ -985,7 +986,7 @@ __device__ int condense_out_regs_mix(const EvalArgs &a, const float *Msm, const 
 // ---------------------------------------------------------------------------
 // shared-memory plan of the evaluation kernel (MIX: float32 contraction with
 // double-float kinematics/law/residual; otherwise everything float64)
-template <int D, int NA, int TA, int TB, int NP, int CI, typename KT>
+template <int D, int NA, int TA, int TB, int NP, int CI, typename KT, bool SYM = false>
 struct Plan {
     static constexpr bool MIX = std::is_same<KT, float>::value;
     static constexpr int G = D * D;
@@ -993,11 +994,15 @@ struct Plan {
     static constexpr int NQ = NA - G;                 // largest n~ served
     static constexpr int QP = NQ | 1;                 // odd row pitch (banks)
     static constexpr int BP = NQ | 1;
-    static constexpr int TPP = (NA / TA) * (NA / TB); // register tiles per point
-    static constexpr int NT = NP * TPP;               // threads per CTA
+    // register tiles per point: all (NA/TA)^2 blocks, or with SYM only the
+    // lower blocks (the augmented system is symmetric)
+    static constexpr int TPP = SYM ? (NA / TA) * (NA / TA + 1) / 2 : (NA / TA) * (NA / TB);
+    static constexpr int NTILE = NP * TPP;            // tile threads
+    static constexpr int NT = ((NTILE > NP * CI ? NTILE : NP * CI) + 31) / 32 * 32;  // threads per CTA
     static constexpr int KC = CI * G;                 // contraction length per chunk
     static constexpr int RPT = (NP * NQ + NT - 1) / NT;
     static_assert(NA % TA == 0 && NA % TB == 0, "tile must divide NA");
+    static_assert(!SYM || TA == TB, "symmetric blocks must be square");
     static_assert(NT % 32 == 0 && NT <= 1024, "bad thread count");
     // 8-byte words (a double, or a double-float pair hi|lo stored as two
     // float arrays of the same length inside the region)
@@ -1032,10 +1037,10 @@ struct Plan {
 };
 
 // ---------------------------------------------------------------------------
-template <int D, int NA, int TA, int TB, int NP, int CI, typename KT, bool ADJ>
-__global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
+template <int D, int NA, int TA, int TB, int NP, int CI, typename KT, bool ADJ, bool SYM = false>
+__global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
     eval_kernel(EvalArgs a) {
-    using PL = Plan<D, NA, TA, TB, NP, CI, KT>;
+    using PL = Plan<D, NA, TA, TB, NP, CI, KT, SYM>;
     constexpr bool MIX = PL::MIX;
     constexpr int G = PL::G, NS = PL::NS, NQ = PL::NQ, QP = PL::QP, BP = PL::BP;
     constexpr int TPP = PL::TPP, NT = PL::NT, KC = PL::KC, RPT = PL::RPT;
@@ -1067,10 +1072,20 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
     const int32_t *perm = a.perm ? a.perm + (a.offset ? *a.offset : 0) : nullptr;
     const int64_t n_tiles = (count + NP - 1) / NP;
 
-    // register tile of the contraction
-    const int tp = tid / TPP;
+    // register tile of the contraction (SYM: lower block (rb, cb), rb >= cb)
+    const bool tiler = tid < PL::NTILE;
+    const int tp = tiler ? tid / TPP : 0;
     const int tt = tid % TPP;
-    const int a0 = (tt / NTB) * TA, b0 = (tt % NTB) * TB;
+    int a0, b0;
+    if (SYM) {
+        int rb = 0;
+        while ((rb + 1) * (rb + 2) / 2 <= tt) ++rb;
+        a0 = rb * TA;
+        b0 = (tt - rb * (rb + 1) / 2) * TB;
+    } else {
+        a0 = (tt / NTB) * TA;
+        b0 = (tt % NTB) * TB;
+    }
     double th[4] = {0.0, 0.0, 0.0, 0.0};  // adjoint: (mu, kappa) of phase 0, phase 1
     // material constants in double-float
     df dmu0{0.0f, 0.0f}, dmu1{0.0f, 0.0f}, dlam0{0.0f, 0.0f}, dlam1{0.0f, 0.0f};
@@ -1352,7 +1367,7 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
             __syncthreads();
 
             // contraction of the augmented system (register tiles)
-            {
+            if (tiler) {
                 const KT *Yp = s_Y + tp * NAP + b0;
 #pragma unroll 4
                 for (int k = 0; k < KC; ++k) {
@@ -1434,11 +1449,13 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT>::NT)
         // lo in the second half of the float view of s_r / s_PU)
         float *s_rh = reinterpret_cast<float *>(s_r), *s_rl = s_rh + NP * NQ;
         float *s_puh = reinterpret_cast<float *>(s_PU), *s_pul = s_puh + NP * G;
+        if (tiler) {
 #pragma unroll
-        for (int x = 0; x < TA; ++x)
+            for (int x = 0; x < TA; ++x)
 #pragma unroll
-            for (int y = 0; y < TB; ++y)
-                s_M[(tp * NA + a0 + x) * NA + b0 + y] = MIX ? (KT)(kh[x][y] - kc[x][y]) : acc[x][y];
+                for (int y = 0; y < TB; ++y)
+                    s_M[(tp * NA + a0 + x) * NA + b0 + y] = MIX ? (KT)(kh[x][y] - kc[x][y]) : acc[x][y];
+        }
         if (MIX) {
 #pragma unroll
             for (int u = 0; u < RPT; ++u) {

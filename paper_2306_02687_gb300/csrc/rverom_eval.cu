@@ -53,22 +53,24 @@ bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) |
 
 #define RV_FUSED(D, NA, TA, TB, NP, CI, KT) &launch_cfg<D, NA, TA, TB, NP, CI, KT, false>
 #define RV_WS(D, NA, TA, TB, NP, CI) &launch_ws<D, NA, TA, TB, NP, CI>
+#define RV_SYM(D, NA, TA, NP, CI, KT) &launch_cfg<D, NA, TA, TA, NP, CI, KT, false, true>
 
 int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out) {
     LaunchFn c[4] = {};
     int k = 0;
     if (dim == 2 && mixed) {
         if (n <= 12) {
+            c[k++] = RV_SYM(2, 16, 4, 24, 10, float);
             c[k++] = RV_FUSED(2, 16, 4, 4, 16, 16, float);
             c[k++] = RV_WS(2, 16, 4, 4, 8, 16);
         } else if (n <= 16) {
-            c[k++] = RV_FUSED(2, 20, 5, 5, 16, 8, float);
-            c[k++] = RV_WS(2, 20, 5, 5, 8, 16);
+            c[k++] = RV_SYM(2, 20, 5, 24, 10, float);
             c[k++] = RV_FUSED(2, 20, 5, 5, 16, 16, float);
+            c[k++] = RV_WS(2, 20, 5, 5, 8, 16);
         } else if (n <= 24) {
+            c[k++] = RV_SYM(2, 28, 7, 24, 10, float);
             c[k++] = RV_FUSED(2, 28, 7, 7, 16, 16, float);
             c[k++] = RV_WS(2, 28, 7, 7, 8, 16);
-            c[k++] = RV_FUSED(2, 28, 7, 7, 16, 8, float);
         } else if (n <= 32) {
             c[k++] = RV_FUSED(2, 36, 9, 9, 16, 8, float);
         } else if (n <= 64) {

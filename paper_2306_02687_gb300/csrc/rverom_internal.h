@@ -27,10 +27,10 @@ namespace rverom {
 
 // Launch one compiled tile configurations <D, NA, TA, TB, NP, CI, KT> as a
 // persistent grid of at most (SMs x resident CTAs) blocks.
-template <int D, int NA, int TA, int TB, int NP, int CI, typename KT, bool ADJ>
+template <int D, int NA, int TA, int TB, int NP, int CI, typename KT, bool ADJ, bool SYM = false>
 cudaError_t launch_cfg(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
-    using PL = Plan<D, NA, TA, TB, NP, CI, KT>;
-    auto kern = eval_kernel<D, NA, TA, TB, NP, CI, KT, ADJ>;
+    using PL = Plan<D, NA, TA, TB, NP, CI, KT, SYM>;
+    auto kern = eval_kernel<D, NA, TA, TB, NP, CI, KT, ADJ, SYM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
     if (e != cudaSuccess) return e;
     int occ = 0;
