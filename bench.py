@@ -143,6 +143,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(ms_local, n_local, world, dist=None, device='cpu'):
+    """Weak-scaling aggregate over ranks: the step time is the maximum over
+    ranks and the throughput counts the points of every rank.  Returns
+    (ms_max, whole-job evaluations per second)."""
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * n_local / (ms * 1e-3)
+
+
 def oracle_rate(rom_paths, types, F, q, s, S, U, budget_s, max_points=None):
     """Evaluations/s of the float64 oracle (single thread) on a bounded sample."""
     from oracle import reduced
@@ -274,12 +287,7 @@ def main():
     with ClockSampler(local) as clk:
         ms_step, ms_kern = timed(args.precision, args.steps, args.warmup)
     clocks = clk.summary()
-    ms_max = ms_step
-    if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = t.item()
-    value = world * n / (ms_max * 1e-3)
+    ms_max, value = aggregate(ms_step, n, world, dist, dev)
 
     # plain float64 GPU form on the same workload (speedup denominator)
     other = 'fp64' if args.precision == 'mixed' else 'mixed'
@@ -317,11 +325,29 @@ def main():
         nrm_pin.copy_(norms, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / e2e_steps
-    if dist:
-        t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = t.item()
+    ms_e2e, e2e_value = aggregate(e0.elapsed_time(e1) / e2e_steps, n, world, dist, dev)
+
+    # the same step captured once in a CUDA graph and replayed
+    restore()
+    step(args.precision)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph):
+            step(args.precision)
+    restore()
+    torch.cuda.synchronize()
+    gms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        graph.replay()
+        g1.record(stream)
+        g1.synchronize()
+        gms += g0.elapsed_time(g1)
+    ms_graph, graph_value = aggregate(gms / args.steps, n, world, dist, dev)
 
     if rank != 0:
         dist.destroy_process_group()
@@ -331,19 +357,22 @@ def main():
     n_per_type = np.bincount(types_np, minlength=len(roms))
     w64 = sum(c * work_per_eval(r)[0] for c, r in zip(n_per_type, roms))
     w32 = sum(c * work_per_eval(r)[1] for c, r in zip(n_per_type, roms))
+    # algorithmic FLOPs (SURVEY 8(d) per evaluation x evaluations per launch)
+    # against the pipe that executes them: the FP64 form runs everything on
+    # the FP64 pipe; the mixed form runs the FP64-accurate part as double-float
+    # and the tangent contraction in float32, both on the FP32 pipe
+    achieved = (w64 + w32) / (ms_kern * 1e-3) / 1e12
     if args.precision == 'fp64':
-        achieved = (w64 + w32) / (ms_kern * 1e-3) / 1e12
-        peak = 1.25
-        bound_unit = 'fp64 pipe'
+        peak, unitname = 1.25, 'FP64 pipe'
+        src = 'nominal: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (measured 1.01 TFLOP/s in a DFMA probe)'
     else:
-        achieved = w64 / (ms_kern * 1e-3) / 1e12
-        peak = 1.25
-        bound_unit = 'fp64 pipe (FP64-accurate F_i, P_i, r, Pbar)'
+        peak, unitname = 80.5, 'FP32 pipe (double-float emulation of the FP64-accurate part)'
+        src = 'nominal: 152 SMs x 128 FFMA/clk x 2 FLOP x 2.07 GHz (measured 74.1 TFLOP/s in an FFMA probe)'
     roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "rverom::eval_kernel", "binding": bound_unit,
-                "peak_source": "nominal FP64 rate 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (no measured FP64 peak in MEASURED_PEAKS.json)",
-                "kernel_ms": ms_kern, "fp32_tflops_achieved": w32 / (ms_kern * 1e-3) / 1e12}
+                "kernel": "rverom::eval_kernel (autotuned configuration)", "binding": unitname,
+                "peak_source": src, "kernel_ms": ms_kern,
+                "algorithmic_flop_per_eval": {"fp64_accurate": w64 / n, "fp32": w32 / n}}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -372,10 +401,12 @@ def main():
                    "failed_points": bad},
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(u_pin.numel() * 8),
                 "d2h_bytes_per_step": int((R_pin.numel() + K_pin.numel() + 3) * 8)},
         "gpu_launches": launches,
+        "graph": {"value": graph_value, "ms_per_step": ms_graph,
+                  "note": "gradient, evaluation, assembly and norms captured in one CUDA graph"},
         "clocks": clocks,
         "other_form": {"precision": other, "value": world * n / (ms_other * 1e-3), "ms_per_step": ms_other},
         "speedup_vs_fp64_form": (ms_other / ms_step) if args.precision == 'mixed' else 1.0,
