@@ -51,6 +51,11 @@ WORKLOADS = {
                desc='2D mixed batch of 3 RVE types (16/32/64 modes, 120/300/600 ECM points), 181x181 Q4 (131044 points)'),
 }
 
+# DRAM traffic per launch of the evaluation kernel from one ncu capture of
+# this workload (profiles/eval_kernel_c2_*_full.md); reported only for that
+# workload and form, and to be refreshed whenever the kernel changes.
+PROFILED_TRAFFIC = {('c2', 'mixed'): 17014528, ('c2', 'fp64'): 17142784}
+
 # algorithmic work per evaluation (FP64 FLOP of kinematics + residual + law,
 # symmetric-half tangent contraction FLOP), per ROM type
 def work_per_eval(rom):
@@ -357,7 +362,7 @@ def main():
     n_per_type = np.bincount(types_np, minlength=len(roms))
     w64 = sum(c * work_per_eval(r)[0] for c, r in zip(n_per_type, roms))
     w32 = sum(c * work_per_eval(r)[1] for c, r in zip(n_per_type, roms))
-    # algorithmic FLOPs (SURVEY 8(d) per evaluation x evaluations per launch)
+    # algorithmic FLOPs (method-required work per evaluation x evaluations per launch)
     # against the pipe that executes them: the FP64 form runs everything on
     # the FP64 pipe; the mixed form runs the FP64-accurate part as double-float
     # and the tangent contraction in float32, both on the FP32 pipe
@@ -369,7 +374,7 @@ def main():
         peak, unitname = 80.5, 'FP32 pipe (double-float emulation of the FP64-accurate part)'
         src = 'nominal: 152 SMs x 128 FFMA/clk x 2 FLOP x 2.07 GHz (measured 74.1 TFLOP/s in an FFMA probe)'
     roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get((args.workload, args.precision)),
                 "kernel": "rverom::eval_kernel (autotuned configuration)", "binding": unitname,
                 "peak_source": src, "kernel_ms": ms_kern,
                 "algorithmic_flop_per_eval": {"fp64_accurate": w64 / n, "fp32": w32 / n}}
