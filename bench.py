@@ -189,6 +189,9 @@ def main():
     ap.add_argument('--precision', default='mixed', choices=['mixed', 'fp64'])
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--candidate', type=int, default=-1,
+                    help='force this forward kernel candidate (rve_rom_select_kernel) for every type and '
+                         'precision after autotuning; -1 keeps the autotuner\'s choice')
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get('RANK', '0'))
@@ -219,6 +222,11 @@ def main():
     roms = [rv.load_rom_file(p) for p in rom_paths]
     h = rv.rve_rom_create(d, roms, roms[0]['V0'])
     tune = {prec: rv.rve_rom_autotune(h, prec, n_sample=16384).round(4).tolist() for prec in ('mixed', 'fp64')}
+    if args.candidate >= 0:
+        for prec in ('mixed', 'fp64'):
+            for t in range(len(roms)):
+                nc = rv.rve_rom_select_kernel(h, t, prec)
+                rv.rve_rom_select_kernel(h, t, prec, min(args.candidate, nc - 1))
     mesh = rv.macro_mesh_create(X, conn)
     n = mesh.n_ip
     types = None
@@ -403,6 +411,7 @@ def main():
                    "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                    "state": "mid-Newton (converged micro state, q perturbed by 1e-3 |q|)",
                    "autotune_ms": tune,
+                   "candidate": args.candidate if args.candidate >= 0 else "autotuned",
                    "failed_points": bad},
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -65,6 +65,11 @@ struct TypeDev {
     const float *wl;   // [m] float32 remainder w - wh
     const int *phase;  // [m]
     double mu[2], kappa[2];
+    // tensor-core path (planar types with n + 4 <= 32): [B_i | I] split into
+    // TF32 leading/trailing parts in the MMA operand layout, per k-step of 8
+    // (k = i * 4 + c): [hi|lo][img_nn / 8][2][8][4] floats
+    const float *Bimg;
+    int img_nn;
 };
 
 // 4-byte asynchronous global -> shared copy (no register round trip)

@@ -54,6 +54,7 @@ bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) |
 #define RV_FUSED(D, NA, TA, TB, NP, CI, KT) &launch_cfg<D, NA, TA, TB, NP, CI, KT, false>
 #define RV_WS(D, NA, TA, TB, NP, CI) &launch_ws<D, NA, TA, TB, NP, CI>
 #define RV_SYM(D, NA, TA, NP, CI, KT) &launch_cfg<D, NA, TA, TA, NP, CI, KT, false, true>
+#define RV_TC(D, NA, NP, CI) &launch_tc<D, NA, NP, CI>
 
 int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out) {
     LaunchFn c[4] = {};
@@ -63,14 +64,17 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out) {
             c[k++] = RV_SYM(2, 16, 4, 24, 10, float);
             c[k++] = RV_FUSED(2, 16, 4, 4, 16, 16, float);
             c[k++] = RV_WS(2, 16, 4, 4, 8, 16);
+            c[k++] = RV_TC(2, 16, 64, 4);
         } else if (n <= 16) {
             c[k++] = RV_SYM(2, 20, 5, 24, 10, float);
             c[k++] = RV_FUSED(2, 20, 5, 5, 16, 16, float);
             c[k++] = RV_WS(2, 20, 5, 5, 8, 16);
+            c[k++] = RV_TC(2, 20, 32, 8);
         } else if (n <= 24) {
             c[k++] = RV_SYM(2, 28, 7, 24, 10, float);
             c[k++] = RV_FUSED(2, 28, 7, 7, 16, 16, float);
             c[k++] = RV_WS(2, 28, 7, 7, 8, 16);
+            c[k++] = RV_TC(2, 28, 32, 8);
         } else if (n <= 32) {
             c[k++] = RV_FUSED(2, 36, 9, 9, 16, 8, float);
         } else if (n <= 64) {
@@ -87,6 +91,38 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out) {
     }
     for (int i = 0; i < k && i < max_out; ++i) out[i] = c[i];
     return k < max_out ? k : max_out;
+}
+
+// float32 value rounded to TF32 (10 fraction bits), ties away from zero
+static float tf32_rna(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float h;
+    std::memcpy(&h, &u, 4);
+    return h;
+}
+
+// B operand image of [B_i | I] for the tensor-core kernels (planar types):
+// per k-step of 8 (k = i * g + c, two ECM points), the TF32 leading part and
+// the trailing part, each [nn/8][2][8][4] (core matrices of 8 columns x 4 k).
+// k-steps past m*g are zero; the count is padded to a multiple of 16.
+static std::vector<float> tc_table_image(const rverom_type_desc &d, int g, int nn) {
+    const int n = d.n_modes, m = d.n_ecm;
+    const int ksteps = ((m * g + 7) / 8 + 15) / 16 * 16;
+    std::vector<float> img((size_t)ksteps * 2 * nn * 8, 0.0f);
+    for (int k = 0; k < m * g; ++k) {
+        const int i = k / g, c = k % g, s = k / 8, kg = (k % 8) / 4, e = k % 4;
+        for (int col = 0; col < n + g; ++col) {
+            const double v = col < n ? d.B[((size_t)i * g + c) * n + col] : (col - n == c ? 1.0 : 0.0);
+            const float hi = tf32_rna((float)v);
+            const float lo = (float)(v - (double)hi);
+            const size_t idx = (size_t)s * 2 * nn * 8 + (col / 8) * 64 + kg * 32 + (col % 8) * 4 + e;
+            img[idx] = hi;
+            img[idx + (size_t)nn * 8] = lo;
+        }
+    }
+    return img;
 }
 
 }  // namespace rverom
@@ -158,6 +194,17 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
         td.wh = wh;
         td.wl = wl;
         td.phase = ph;
+        td.Bimg = nullptr;
+        td.img_nn = 0;
+        if (ok && dim == 2 && d.n_modes + g <= 32) {
+            const int nn = (d.n_modes + g + 15) / 16 * 16;
+            std::vector<float> img = tc_table_image(d, g, nn);
+            float *bi = nullptr;
+            ok = cudaMalloc(&bi, img.size() * sizeof(float)) == cudaSuccess &&
+                 cudaMemcpy(bi, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+            td.Bimg = bi;
+            td.img_nn = nn;
+        }
         for (int k = 0; k < 2; ++k) {
             td.mu[k] = d.moduli[k][0];
             td.kappa[k] = d.moduli[k][1];
@@ -170,6 +217,8 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
             cudaFree(wl);
             cudaFree(w);
             cudaFree(ph);
+            cudaFree((void *)td.Bimg);
+            td.Bimg = nullptr;
             td.Bh = nullptr;
             td.Bl = nullptr;
             td.wh = nullptr;
@@ -201,6 +250,7 @@ extern "C" int rve_rom_destroy(rverom_t h) {
         cudaFree((void *)h->types[t].wl);
         cudaFree((void *)h->types[t].w);
         cudaFree((void *)h->types[t].phase);
+        cudaFree((void *)h->types[t].Bimg);
     }
     cudaFree(h->bucket_small);
     cudaFree(h->perm);

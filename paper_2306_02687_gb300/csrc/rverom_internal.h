@@ -6,6 +6,7 @@
 #include "../../include/rverom.h"
 #include "rom_core.cuh"
 #include "rom_ws.cuh"
+#include "rom_tc.cuh"
 
 struct rverom_s {
     int dim = 2;
@@ -59,6 +60,24 @@ cudaError_t launch_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaStrea
     if (occ < 1) occ = 1;
     int64_t tiles = (max_points + NP - 1) / NP;
     int64_t grid = (int64_t)n_sm * occ;
+    if (tiles < grid) grid = tiles;
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = (int)grid;
+    kern<<<(unsigned)grid, PL::NT, PL::bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Tensor-core mixed-precision forward kernel <D, NA, NP, CI>: one CTA per
+// SM (its shared memory and TMEM allocation fill the SM).
+template <int D, int NA, int NP, int CI>
+cudaError_t launch_tc(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
+    using PL = TcPlan<D, NA, NP, CI>;
+    if (!a.t.Bimg || a.t.img_nn != PL::NN) return cudaErrorInvalidValue;
+    auto kern = eval_tc_kernel<D, NA, NP, CI>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
+    if (e != cudaSuccess) return e;
+    int64_t tiles = (max_points + NP - 1) / NP;
+    int64_t grid = n_sm;
     if (tiles < grid) grid = tiles;
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;

@@ -309,3 +309,47 @@ def test_every_tile_configuration_matches_oracle(names):
         ms = rv.rve_rom_autotune(h, precision, n_sample=2048)
         assert np.all(ms[:, 0] > 0)
         compare(run_gpu(h, F, q, s, S, U, precision, types=types), outs, h.nmax, tol)
+
+
+@pytest.mark.parametrize('name', ['c1', 'c2'])
+def test_tensor_core_kernel_many_tiles(name):
+    # the tcgen05 candidate (last in the list) over several tiles per CTA and
+    # a ragged tail: element-wise against the SIMT mixed kernel on every
+    # point, and against the oracle on sampled mid-Newton points
+    import os
+    if not os.path.exists(rom_path(name)):
+        pytest.skip('ROM file not generated')
+    h, oroms = _handle([name])
+    orom = oroms[0]
+    nc = rv.rve_rom_select_kernel(h, 0, 'mixed')
+    assert nc == 4
+    n = 2 * 152 * 64 + 13
+    idx = np.sort(syn.rng(11).choice(n, 24, replace=False))
+    F = syn.fbar_batch(syn.SEED_BASE + 40, 2, n, 0.1, 0.3)
+    q = np.zeros((n, h.nmax))
+    s = np.zeros((n, h.nmax))
+    S = np.zeros((n, h.nmax, 3))
+    U = np.tile([1.0, 1.0, 0.0], (n, 1))
+    # mid-Newton states everywhere: micro Newton iterations at fixed F with
+    # the float64 form, then a relative perturbation of q (the mixed-form
+    # error is a fraction of the Newton correction, so fresh states far from
+    # equilibrium would compare the two kernels' float32 solve errors)
+    rv.rve_rom_select_kernel(h, 0, 'fp64', 0)
+    for _ in range(4):
+        g = run_gpu(h, F, q, s, S, U, 'fp64')
+        q, s, S, U = g['q'], g['s'], g['S'], g['Uprev']
+    q = q + syn.perturbation(syn.SEED_BASE + 42, q.shape, 1.0) * 1e-3 * np.abs(q).max(axis=1, keepdims=True)
+    Fm, qm, sm, Sm, Um = mid_newton_inputs(orom, len(idx), syn.SEED_BASE + 41)
+    F[idx], q[idx], s[idx], S[idx], U[idx] = Fm, qm, sm, Sm, Um
+    rv.rve_rom_select_kernel(h, 0, 'mixed', 0)
+    ref = run_gpu(h, F, q, s, S, U, 'mixed')
+    rv.rve_rom_select_kernel(h, 0, 'mixed', nc - 1)
+    g = run_gpu(h, F, q, s, S, U, 'mixed')
+    assert np.all(g['status'] == 0) and np.all(ref['status'] == 0)
+    scale = np.abs(ref['Pbar']).max(axis=1)
+    assert np.max(np.abs(g['Pbar'] - ref['Pbar']).max(axis=1) / scale) <= 2e-8
+    tscale = np.abs(ref['dPdF']).max(axis=(1, 2))
+    assert np.max(np.abs(g['dPdF'] - ref['dPdF']).max(axis=(1, 2)) / tscale) <= 2e-5
+    assert np.array_equal(g['q'], ref['q']) and np.array_equal(g['Uprev'], ref['Uprev'])
+    compare({k: v[idx] for k, v in g.items()}, oracle_batch(oroms, F[idx], q[idx], s[idx], S[idx], U[idx]),
+            h.nmax, TOL_MIXED)
