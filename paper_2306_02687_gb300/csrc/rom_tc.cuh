@@ -7,8 +7,15 @@
 // is computed for all points of a CTA at once as one matrix product whose
 // shared operand is the gradient table:
 //     D[(alpha, j), c] = sum_k Y[k, (alpha, j)] Bext[k, c],   k = (i, component)
-// A operand: the Y rows of the CTA's points stacked along M (NAR rows per
-//            point, 128-row MMA tiles), built in shared memory per k-step.
+// A operand: the Y rows of the CTA's points stacked along M (16 or 32 rows
+//            per point, one 128-row MMA tile per warp), built in shared
+//            memory per k-step of 8.
+// Work split: each warp owns one tile (PPT points) for the whole ECM loop:
+// it evaluates the law for its points, builds its A rows, issues and commits
+// its own MMAs and accumulates its points' residual, so a k-step needs only
+// warp-level synchronization; the only CTA barrier per chunk of ECM points
+// comes with the fold of the TMEM accumulators, where a warp reads one lane
+// quarter of every tile.
 // B operand: Bext, pre-split on the host into TF32 leading and trailing parts
 //            and pre-arranged in the MMA's core-matrix layout, so that a chunk
 //            of ECM points is one contiguous bulk (TMA) copy.
@@ -38,41 +45,36 @@ struct TcPlan {
     static constexpr int NQ = NA - G;
     static constexpr int QP = NQ | 1;
     static constexpr int BP = NQ | 1;
-    static constexpr int NAR = (NA + 7) / 8 * 8;    // A-operand rows per point
+    static constexpr int NAR = NA <= 16 ? 16 : 32;  // A-operand rows per point
+    static constexpr int PPT = 128 / NAR;           // points per 128-row tile
     static constexpr int NN = (NA + 15) / 16 * 16;  // MMA N (columns of Bext)
-    static constexpr int ROWS = NP * NAR;
-    static constexpr int MT = (ROWS + 127) / 128;   // 128-row MMA tiles
-    static constexpr int MROWS = MT * 128;
+    static constexpr int NT = 256;
+    static constexpr int NW = NT / 32;              // warps = tiles
     static constexpr int EPS = 8 / G;               // ECM points per k-step of 8
     static constexpr int KSC = CI / EPS;            // k-steps per chunk
-    static constexpr int NT = 256;
-    static constexpr int RPT = (NP * NQ + NT - 1) / NT;
-    // chunks per fold group: the tensor core's float32 accumulation does not
-    // round to nearest (it behaves like truncation), so its accumulator is
-    // restarted every chunk (at most 3 * KSC MMAs) and the chunk results are
-    // added, rounded to nearest, into the running sum
-    static constexpr int FG = 1;
-    static constexpr int TCOLS = 2 * MT * NN;       // accumulator + running sum
+    static constexpr int RPW = (PPT * NQ + 31) / 32;  // residual outputs per lane
+    static constexpr int TCOLS = 2 * NW * NN;       // accumulator + running sum
     static constexpr int TALLOC = TCOLS <= 32 ? 32 : TCOLS <= 64 ? 64 : TCOLS <= 128 ? 128 : TCOLS <= 256 ? 256 : 512;
-    static_assert(D == 2, "planar RVEs (one or two ECM points per k-step)");
+    static_assert(D == 2, "planar RVEs (two ECM points per k-step)");
+    static_assert(NA <= 32, "register-resident condensation");
+    static_assert(NP == NW * PPT, "one tile per warp");
+    static_assert(CI * PPT == 32, "one law evaluation per lane and chunk");
     static_assert(CI % EPS == 0, "a chunk holds whole k-steps");
     static_assert(TCOLS <= 512, "TMEM holds 512 columns");
-    static_assert(NA <= 32, "register-resident condensation");
-    static_assert(NP * CI >= NT / 2, "law phase keeps most threads busy");
     // byte offsets
-    static constexpr size_t YPART = (size_t)MT * 4096;  // one k-step, one part (hi or lo)
+    static constexpr size_t YWARP = 4 * 4096;  // per warp: [2 buffers][hi|lo][2 kg][16 rg][8][4] floats
     static constexpr size_t MBYTES = (size_t)NP * NA * NA * 4;
-    static constexpr size_t o_Y = 0;  // [2 buffers][hi|lo][MT][2 kg][16 rg][8][4]; later M[NP][NA][NA]
-    static constexpr size_t BXPART = (size_t)NN * 32;    // [NN/8][2 kg][8][4] floats
+    static constexpr size_t o_Y = 0;  // later M[NP][NA][NA]
+    static constexpr size_t BXPART = (size_t)NN * 32;  // [NN/8][2 kg][8][4] floats
     static constexpr size_t BXBUF = (size_t)KSC * 2 * BXPART;
-    static constexpr size_t o_BX = tc_al(o_Y + (4 * YPART > MBYTES ? 4 * YPART : MBYTES));
+    static constexpr size_t o_BX = tc_al(o_Y + (NW * YWARP > MBYTES ? NW * YWARP : MBYTES));
     static constexpr size_t NBST = (size_t)CI * G * BP;  // floats per part of a staging buffer
     static constexpr size_t o_B = tc_al(o_BX + 2 * BXBUF);
     static constexpr size_t o_w = tc_al(o_B + 2 * 2 * NBST * 4);
     static constexpr size_t o_ph = tc_al(o_w + 2 * 2 * CI * 4);
-    static constexpr size_t o_W = tc_al(o_ph + 2 * CI * 4);
-    static constexpr size_t o_WP = tc_al(o_W + (size_t)CI * NP * G * G * 4);
-    static constexpr size_t o_q = tc_al(o_WP + 2 * (size_t)CI * G * NP * 4);
+    static constexpr size_t o_W = tc_al(o_ph + 2 * CI * 4);            // [warp][il][p][G*G]
+    static constexpr size_t o_WP = tc_al(o_W + (size_t)NP * CI * G * G * 4);  // hi | lo: [warp][il][c][p]
+    static constexpr size_t o_q = tc_al(o_WP + 2 * (size_t)NP * CI * G * 4);
     static constexpr size_t o_q64 = tc_al(o_q + 2 * (size_t)NP * QP * 4);
     static constexpr size_t o_U = tc_al(o_q64 + (size_t)NP * QP * 8);
     static constexpr size_t o_R = tc_al(o_U + (size_t)NP * G * 8);
@@ -82,30 +84,29 @@ struct TcPlan {
     static constexpr size_t o_PU = tc_al(o_r + 2 * (size_t)NP * NQ * 4);
     static constexpr size_t o_flag = tc_al(o_PU + 2 * (size_t)NP * G * 4);
     static constexpr size_t o_pidx = o_flag + NP * 4;
-    static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);  // 4 mbarriers, TMEM slot, error flag
-    static constexpr size_t bytes = o_bar + 64;
+    // mbarriers: [0,1] table copies, [2 + 2 w + b] MMA commits of warp w; then TMEM slot, error flag
+    static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);
+    static constexpr size_t o_slot = o_bar + (2 + 2 * NW) * 8;
+    static constexpr size_t bytes = tc_al(o_slot + 8);
     static_assert(bytes <= 227 * 1024, "shared memory");
 };
 
-// Image of Bext for the B operand: per k-step of 8 (k = i * G + c), the TF32
-// leading part then the trailing part, each [nn/8][2][8][4] floats.
-// Defined with the host-side table preparation.
+// Bext image for the B operand: per k-step of 8 (k = i * G + c), the TF32
+// leading part then the trailing part, each [nn/8][2][8][4] floats (built by
+// the host when the ROM is loaded).
 template <int D, int NA, int NP, int CI>
 __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     using PL = TcPlan<D, NA, NP, CI>;
     constexpr int G = PL::G, NS = PL::NS, NQ = PL::NQ, QP = PL::QP, BP = PL::BP;
-    constexpr int NAR = PL::NAR, NN = PL::NN, MT = PL::MT, MROWS = PL::MROWS;
-    constexpr int EPS = PL::EPS, KSC = PL::KSC, NT = PL::NT, RPT = PL::RPT;
+    constexpr int NAR = PL::NAR, PPT = PL::PPT, NN = PL::NN, NW = PL::NW;
+    constexpr int EPS = PL::EPS, KSC = PL::KSC, NT = PL::NT, RPW = PL::RPW;
     constexpr int NBST = (int)PL::NBST;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    float *s_Y = reinterpret_cast<float *>(smem + PL::o_Y);
+    extern __shared__ __align__(16) unsigned char smem[];
     float *s_Mf = reinterpret_cast<float *>(smem + PL::o_Y);
     float *s_BX = reinterpret_cast<float *>(smem + PL::o_BX);
     float *s_Bst = reinterpret_cast<float *>(smem + PL::o_B);
     float *s_wst = reinterpret_cast<float *>(smem + PL::o_w);
     int *s_ph = reinterpret_cast<int *>(smem + PL::o_ph);
-    float *s_W = reinterpret_cast<float *>(smem + PL::o_W);
-    float *s_WPh = reinterpret_cast<float *>(smem + PL::o_WP), *s_WPl = s_WPh + CI * G * NP;
     float *s_qh = reinterpret_cast<float *>(smem + PL::o_q), *s_ql = s_qh + NP * QP;
     double *s_qd = reinterpret_cast<double *>(smem + PL::o_q64);
     double *s_U = reinterpret_cast<double *>(smem + PL::o_U);
@@ -116,9 +117,9 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     float *s_puh = reinterpret_cast<float *>(smem + PL::o_PU), *s_pul = s_puh + NP * G;
     int *s_flag = reinterpret_cast<int *>(smem + PL::o_flag);
     int *s_pidx = reinterpret_cast<int *>(smem + PL::o_pidx);
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + PL::o_bar);  // [0,1] table copies, [2,3] MMA commits
-    uint32_t *s_slot = reinterpret_cast<uint32_t *>(smem + PL::o_bar + 32);
-    int *s_err = reinterpret_cast<int *>(smem + PL::o_bar + 36);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + PL::o_bar);
+    uint32_t *s_slot = reinterpret_cast<uint32_t *>(smem + PL::o_slot);
+    int *s_err = reinterpret_cast<int *>(smem + PL::o_slot + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n = a.t.n, m = a.t.m;
@@ -127,6 +128,14 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     const int32_t *perm = a.perm ? a.perm + (a.offset ? *a.offset : 0) : nullptr;
     const int64_t n_tiles = (count + NP - 1) / NP;
     const int nch = (m + CI - 1) / CI;
+    // this warp's tile: points p0 .. p0 + PPT - 1 of the CTA, its A rows, its
+    // TMEM accumulator columns, its MMA commit barriers
+    const int p0 = warp * PPT;
+    float *yw = reinterpret_cast<float *>(smem + PL::o_Y + warp * PL::YWARP);
+    float *Ww = reinterpret_cast<float *>(smem + PL::o_W) + warp * CI * PPT * G * G;
+    float *WPh = reinterpret_cast<float *>(smem + PL::o_WP) + warp * CI * G * PPT;
+    float *WPl = WPh + NP * CI * G;
+    uint64_t *mbar = s_bar + 2 + 2 * warp;
 
     const df dmu0 = df_from(a.t.mu[0]), dmu1 = df_from(a.t.mu[1]);
     const df dlam0 = df_from(a.t.kappa[0] - (2.0 / 3.0) * a.t.mu[0]);
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int b = 0; b < 4; ++b) tc::mbar_init(&s_bar[b], 1);
+        for (int b = 0; b < 2 + 2 * NW; ++b) tc::mbar_init(&s_bar[b], 1);
         tc::mbar_init_fence();
         *s_err = 0;
     }
@@ -236,33 +245,36 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             s_qh[p * QP + j] = v.hi;
             s_ql[p * QP + j] = v.lo;
         }
-        dacc rdacc[2 * RPT];
+        dacc rdacc[2 * RPW];
 #pragma unroll
-        for (int u = 0; u < 2 * RPT; ++u) rdacc[u] = dacc{0.0f, 0.0f};
+        for (int u = 0; u < 2 * RPW; ++u) rdacc[u] = dacc{0.0f, 0.0f};
         df pudf{0.0f, 0.0f};
+        // first chunk's tables
+        stage_cp(gchunk & 1, 0);
+        if (tid == 0) stage_bulk(gchunk & 1, 0);
+        cp_async_wait<0>();
         __syncthreads();
 
         // ---- ECM loop: a2-a5 ----------------------------------------------
-        stage_cp(gchunk & 1, 0);
-        if (tid == 0) stage_bulk(gchunk & 1, 0);
-        bool fresh = true;  // the next MMA starts a fold group
         int folds = 0;
         for (int ch = 0; ch < nch; ++ch, ++gchunk) {
             const int buf = gchunk & 1;
             const int i0 = ch * CI;
+            // prefetch the next chunk: its staging buffer and table image were
+            // last read in chunk ch-1, which every warp finished (the MMAs too)
+            // before the barrier that closed it
             if (ch + 1 < nch) {
                 stage_cp(buf ^ 1, i0 + CI);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
+                if (tid == 0) stage_bulk(buf ^ 1, ch + 1);
             }
-            __syncthreads();
             const float *Bh = s_Bst + buf * 2 * NBST, *Bl = Bh + NBST;
             const float *wh = s_wst + buf * 2 * CI, *wl = wh + CI;
 
-            // pointwise: F_i, law, w P_i (double-float), W_i = w_i A_i (float32)
-            for (int task = tid; task < NP * CI; task += NT) {
-                const int p = task % NP, il = task / NP;
+            // pointwise (this warp's points, one ECM point per lane):
+            // F_i, law, w P_i (double-float), W_i = w_i A_i (float32)
+            {
+                const int pl = lane % PPT, il = lane / PPT;
+                const int p = p0 + pl;
                 bool live = (s_flag[p] == ST_OK) && (i0 + il < m);
                 const int ph = s_ph[buf * CI + il];
                 float fi[G];
@@ -289,12 +301,12 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
 #pragma unroll
                         for (int c = 0; c < G; ++c) {
                             const df wp = df_mul(w2, P[c]);
-                            s_WPh[(il * G + c) * NP + p] = wp.hi;
-                            s_WPl[(il * G + c) * NP + p] = wp.lo;
+                            WPh[(il * G + c) * PPT + pl] = wp.hi;
+                            WPl[(il * G + c) * PPT + pl] = wp.lo;
                         }
                     }
                 }
-                float *Wt = s_W + (il * NP + p) * G * G;
+                float4 *Wt = reinterpret_cast<float4 *>(Ww + (il * PPT + pl) * G * G);
                 if (live) {
                     const float muk = ph ? kmu1 : kmu0, lam = ph ? klam1 : klam0;
                     const float c3 = muk - lam * lnJk;
@@ -303,169 +315,168 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     for (int c = 0; c < G; ++c) {
                         float Ar[G];
                         nh_tangent_row<D, float>(fi, lam, c3, muk, c, Ar);
-#pragma unroll
-                        for (int e = 0; e < G; ++e) Wt[c * G + e] = wk * Ar[e];
+                        Wt[c] = make_float4(wk * Ar[0], wk * Ar[1], wk * Ar[2], wk * Ar[3]);
                     }
                 } else {
 #pragma unroll
                     for (int c = 0; c < G; ++c) {
-                        s_WPh[(il * G + c) * NP + p] = 0.0f;
-                        s_WPl[(il * G + c) * NP + p] = 0.0f;
+                        WPh[(il * G + c) * PPT + pl] = 0.0f;
+                        WPl[(il * G + c) * PPT + pl] = 0.0f;
+                        Wt[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     }
-#pragma unroll
-                    for (int e = 0; e < G * G; ++e) Wt[e] = 0.0f;
                 }
             }
-            __syncthreads();
-            // next chunk's table image; its buffer was last read by the MMAs of chunk ch-1
-            if (tid == 0 && ch + 1 < nch) {
-                if (ch > 0 && !tc::mbar_wait(&s_bar[2 + ((gstep - 1) & 1)], ((gstep - 1) >> 1) & 1)) *s_err = 1;
-                stage_bulk(buf ^ 1, ch + 1);
-            }
+            __syncwarp();
 
-            // a5: per k-step, build Y (A operand) and issue the MMAs
+            // a5: per k-step, this warp builds its tile's A rows and issues
+            // its three MMAs (D_tile += Yhi Bhi + Yhi Blo + Ylo Bhi)
+            const int j = lane % NAR;  // row within the point (the same for all of this lane's rows)
             for (int ks = 0; ks < KSC; ++ks) {
                 const uint32_t s = gstep + ks;
                 const int yb = s & 1;
-                if (s >= 2 && !tc::mbar_wait(&s_bar[2 + yb], ((s - 2) >> 1) & 1)) *s_err = 1;
-                float *Yh = s_Y + yb * 2 * (PL::YPART / 4), *Yl = Yh + PL::YPART / 4;
-                for (int task = tid; task < EPS * MROWS; task += NT) {
-                    const int r = task % MROWS, e = task / MROWS;
+                if (s >= 2 && !tc::mbar_wait(&mbar[yb], ((s - 2) >> 1) & 1)) *s_err = 1;
+                float *Yh = yw + yb * 2048, *Yl = Yh + 1024;
+#pragma unroll
+                for (int e = 0; e < EPS; ++e) {
                     const int il = ks * EPS + e;
-                    const int p = r / NAR, j = r - p * NAR;
-                    float y[G];
+                    float bx[G];
 #pragma unroll
-                    for (int c = 0; c < G; ++c) y[c] = 0.0f;
-                    if (p < NP && j < na) {
-                        const float *Wt = s_W + (il * NP + p) * G * G;
-                        float bx[G];
+                    for (int d = 0; d < G; ++d) bx[d] = (j < n) ? Bh[(il * G + d) * BP + j] : ((j - n == d) ? 1.0f : 0.0f);
+                    const bool jin = j < na;
 #pragma unroll
-                        for (int d = 0; d < G; ++d) bx[d] = (j < n) ? Bh[(il * G + d) * BP + j] : ((j - n == d) ? 1.0f : 0.0f);
+                    for (int k = 0; k < 4; ++k) {
+                        const int rl = k * 32 + lane;  // row within the tile
+                        const int pl = rl / NAR;
+                        const float4 *Wt = reinterpret_cast<const float4 *>(Ww + (il * PPT + pl) * G * G);
+                        float y[G];
 #pragma unroll
                         for (int c = 0; c < G; ++c) {
-                            float v = 0.0f;
-#pragma unroll
-                            for (int d = 0; d < G; ++d) v = __fmaf_rn(Wt[c * G + d], bx[d], v);
-                            y[c] = v;
+                            const float4 wv = Wt[c];
+                            float v = wv.x * bx[0];
+                            v = __fmaf_rn(wv.y, bx[1], v);
+                            v = __fmaf_rn(wv.z, bx[2], v);
+                            v = __fmaf_rn(wv.w, bx[3], v);
+                            y[c] = jin ? v : 0.0f;
                         }
-                    }
-                    float hi[G], lo[G];
+                        float hi[G], lo[G];
 #pragma unroll
-                    for (int c = 0; c < G; ++c) tc::split_tf32(y[c], hi[c], lo[c]);
-                    const int off = (r >> 7) * 1024 + e * 512 + (r & 127) * 4;
-                    *reinterpret_cast<float4 *>(Yh + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-                    *reinterpret_cast<float4 *>(Yl + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                        for (int c = 0; c < G; ++c) tc::split_tf32(y[c], hi[c], lo[c]);
+                        const int off = e * 512 + rl * 4;
+                        *reinterpret_cast<float4 *>(Yh + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                        *reinterpret_cast<float4 *>(Yl + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                    }
                 }
                 tc::fence_proxy_async();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::fence_after_sync();
+                __syncwarp();
+                if (lane == 0) {
                     if (ks == 0 && !tc::mbar_wait(&s_bar[buf], (gchunk >> 1) & 1)) *s_err = 1;
-                    const uint32_t ya = tc::smem_u32(Yh), yla = tc::smem_u32(Yl);
+                    tc::fence_after_sync();
                     const uint32_t ba = tc::smem_u32(s_BX + buf * (PL::BXBUF / 4) + ks * 2 * (PL::BXPART / 4));
                     const uint64_t bdh = tc::smem_desc(ba, 128, 256);
                     const uint64_t bdl = tc::smem_desc(ba + (uint32_t)PL::BXPART, 128, 256);
-#pragma unroll 1
-                    for (int t = 0; t < MT; ++t) {
-                        const uint32_t dt = tbase + t * NN;
-                        const uint64_t adh = tc::smem_desc(ya + t * 4096, 2048, 128);
-                        const uint64_t adl = tc::smem_desc(yla + t * 4096, 2048, 128);
-                        tc::mma_tf32(dt, adh, bdh, idesc, fresh ? 0u : 1u);
-                        tc::mma_tf32(dt, adh, bdl, idesc, 1u);
-                        tc::mma_tf32(dt, adl, bdh, idesc, 1u);
-                    }
-                    tc::mma_commit(&s_bar[2 + yb]);
+                    const uint64_t adh = tc::smem_desc(tc::smem_u32(Yh), 2048, 128);
+                    const uint64_t adl = tc::smem_desc(tc::smem_u32(Yl), 2048, 128);
+                    const uint32_t dt = tbase + warp * NN;
+                    tc::mma_tf32(dt, adh, bdh, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_tf32(dt, adh, bdl, idesc, 1u);
+                    tc::mma_tf32(dt, adl, bdh, idesc, 1u);
+                    tc::mma_commit(&mbar[yb]);
                 }
-                fresh = false;
+                __syncwarp();
             }
             gstep += KSC;
 
-            // a4: float64-accurate reduced residual and homogenized stress
+            // a4: float64-accurate reduced residual and homogenized stress of
+            // this warp's points
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                const int o = tid + u * NT;
-                if (o < NP * NQ) {
-                    const int p = o / NQ, j = o % NQ;
-                    if (j < n) {
+            for (int u = 0; u < RPW; ++u) {
+                const int o = lane + 32 * u;
+                if (o < PPT * NQ) {
+                    const int pl = o / NQ, jj = o % NQ;
+                    if (jj < n) {
                         dacc v0 = rdacc[2 * u], v1 = rdacc[2 * u + 1];
                         for (int il = 0; il < CI; il += 2)
 #pragma unroll
                             for (int c = 0; c < G; ++c) {
-                                const int b0 = (il * G + c) * BP + j, w0 = (il * G + c) * NP + p;
-                                const int b1 = b0 + G * BP, w1 = w0 + G * NP;
-                                dacc_fma(v0, Bh[b0], Bl[b0], s_WPh[w0], s_WPl[w0]);
-                                dacc_fma(v1, Bh[b1], Bl[b1], s_WPh[w1], s_WPl[w1]);
+                                const int b0 = (il * G + c) * BP + jj, w0 = (il * G + c) * PPT + pl;
+                                const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
+                                dacc_fma(v0, Bh[b0], Bl[b0], WPh[w0], WPl[w0]);
+                                dacc_fma(v1, Bh[b1], Bl[b1], WPh[w1], WPl[w1]);
                             }
                         rdacc[2 * u] = v0;
                         rdacc[2 * u + 1] = v1;
                     }
                 }
             }
-            if (tid < NP * G) {
-                const int p = tid / G, c = tid % G;
+            if (lane < PPT * G) {
+                const int pl = lane / G, c = lane % G;
                 for (int il = 0; il < CI; ++il)
-                    pudf = df_add(pudf, df{s_WPh[(il * G + c) * NP + p], s_WPl[(il * G + c) * NP + p]});
+                    pudf = df_add(pudf, df{WPh[(il * G + c) * PPT + pl], WPl[(il * G + c) * PPT + pl]});
             }
 
-            // fold the group accumulator into the running sum (TMEM); the last
-            // fold writes the augmented system of every point to shared memory
+            // fold the chunk accumulators into the running sums (TMEM); the
+            // last fold writes the augmented system of every point to shared
+            // memory.  A warp reads its lane quarter of every other tile, so it
+            // waits for the last commit of every warp.
             const bool last = (ch == nch - 1);
-            if ((ch + 1) % PL::FG == 0 || last) {
+            {
                 const uint32_t sl = gstep - 1;
-                if (!tc::mbar_wait(&s_bar[2 + (sl & 1)], (sl >> 1) & 1)) *s_err = 1;
+                for (int w2 = 0; w2 < NW; ++w2)
+                    if (!tc::mbar_wait(&s_bar[2 + 2 * w2 + (sl & 1)], (sl >> 1) & 1)) *s_err = 1;
                 __syncwarp();  // the TMEM loads below are warp-collective
                 tc::fence_after_sync();
                 const int qd = warp & 3;
                 const uint32_t lanes = (uint32_t)(qd * 32) << 16;
-                for (int t = warp >> 2; t < MT; t += 2) {
+                for (int t = warp >> 2; t < NW; t += 2) {
                     const int row = t * 128 + qd * 32 + lane;
-                    const int p = row / NAR, j = row - p * NAR;
+                    const int p = row / NAR, jr = row % NAR;
 #pragma unroll
                     for (int cb = 0; cb < NN / 16; ++cb) {
                         float va[16], vs[16];
                         tc::tmem_ld16(tbase + lanes + t * NN + cb * 16, va);
-                        if (folds > 0) tc::tmem_ld16(tbase + lanes + MT * NN + t * NN + cb * 16, vs);
+                        if (folds > 0) tc::tmem_ld16(tbase + lanes + NW * NN + t * NN + cb * 16, vs);
                         tc::tmem_wait_ld();
                         if (folds > 0) {
 #pragma unroll
                             for (int c = 0; c < 16; ++c) va[c] = __fadd_rn(vs[c], va[c]);
                         }
                         if (!last) {
-                            tc::tmem_st16(tbase + lanes + MT * NN + t * NN + cb * 16, va);
-                        } else if (p < NP && j < NA) {
+                            tc::tmem_st16(tbase + lanes + NW * NN + t * NN + cb * 16, va);
+                        } else if (jr < NA) {
 #pragma unroll
                             for (int c = 0; c < 16; ++c) {
                                 const int col = cb * 16 + c;
-                                if (col < NA) s_Mf[(p * NA + col) * NA + j] = va[c];
+                                if (col < NA) s_Mf[(p * NA + col) * NA + jr] = va[c];
                             }
                         }
                     }
                 }
                 if (!last) tc::tmem_wait_st();
-                tc::fence_before_sync();
-                fresh = true;
                 ++folds;
             }
+            tc::fence_before_sync();
+            if (ch + 1 < nch) cp_async_wait<0>();
             __syncthreads();
+            tc::fence_after_sync();
         }
 
         // ---- spill the residual and Pbar_U (double-float pairs) -------------
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            const int o = tid + u * NT;
-            if (o < NP * NQ) {
+        for (int u = 0; u < RPW; ++u) {
+            const int o = lane + 32 * u;
+            if (o < PPT * NQ) {
                 const df v = df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1]));
-                s_rh[o] = v.hi;
-                s_rl[o] = v.lo;
+                s_rh[p0 * NQ + o] = v.hi;
+                s_rl[p0 * NQ + o] = v.lo;
             }
         }
-        if (tid < NP * G) {
-            s_puh[tid] = pudf.hi;
-            s_pul[tid] = pudf.lo;
+        if (lane < PPT * G) {
+            s_puh[p0 * G + lane] = pudf.hi;
+            s_pul[p0 * G + lane] = pudf.lo;
         }
         __syncthreads();
         // ---- a6, a7: condensation and outputs, one warp per point -----------
-        for (int p = warp; p < NP; p += NT / 32) {
+        for (int p = warp; p < NP; p += NW) {
             const int gp = s_pidx[p];
             if (gp < 0) continue;
             condense_out_regs_mix<D, NA, NQ>(a, s_Mf + p * NA * NA, s_rh + p * NQ, s_rl + p * NQ, s_puh + p * G,
