@@ -97,6 +97,9 @@ struct EvalArgs {
     const double *gP;   // [n][g] cotangent on Pbar
     double *gF;         // [n][g] cotangent on Fbar (out)
     double *partials;   // [gridDim.x][4] per-CTA sums of the moduli gradient
+    // tensor-core form only: per-point workspace records, indexed by the
+    // point's position in the (bucketed) batch
+    float *cond;
 };
 
 // ---------------------------------------------------------------------------

@@ -20,15 +20,18 @@
 //            and pre-arranged in the MMA's core-matrix layout, so that a chunk
 //            of ECM points is one contiguous bulk (TMA) copy.
 // Precision: three TF32 products per k-step (Yhi Bhi + Yhi Blo + Ylo Bhi)
-// give float32-level products; the float32 accumulator in TMEM is started
-// fresh every chunk of CI ECM points and added into a running sum (also in
-// TMEM), which bounds the accumulation error like the compensated chunk sums
-// of the SIMT kernel.
-// Everything else (a1-a4, a6, a7) is the mixed form of the SIMT kernel:
-// double-float kinematics, law, residual and homogenized stress; float32
-// tangent and factorization; register-resident condensation.
+// give float32-level products; the tensor core's float32 accumulation (which
+// does not round to nearest) runs over one chunk of CI ECM points only, and
+// the chunk sums are added into a running sum (also in TMEM) with Kahan
+// compensation, like the compensated chunk sums of the SIMT kernel.
+// Steps a1-a4 are the mixed form of the SIMT kernel (double-float
+// kinematics, law, residual and homogenized stress; float32 tangent).  The
+// kernel ends with a per-point workspace record (the augmented system, the
+// right-hand side, the micro state, the polar factors); condense_kernel
+// then performs steps a6 and a7 with one thread per point.
 #pragma once
 
+#include "rom_condense.cuh"
 #include "rom_core.cuh"
 #include "tc.cuh"
 
@@ -63,11 +66,10 @@ struct TcPlan {
     static_assert(TCOLS <= 512, "TMEM holds 512 columns");
     // byte offsets
     static constexpr size_t YWARP = 4 * 4096;  // per warp: [2 buffers][hi|lo][2 kg][16 rg][8][4] floats
-    static constexpr size_t MBYTES = (size_t)NP * NA * NA * 4;
-    static constexpr size_t o_Y = 0;  // later M[NP][NA][NA]
+    static constexpr size_t o_Y = 0;
     static constexpr size_t BXPART = (size_t)NN * 32;  // [NN/8][2 kg][8][4] floats
     static constexpr size_t BXBUF = (size_t)KSC * 2 * BXPART;
-    static constexpr size_t o_BX = tc_al(o_Y + (NW * YWARP > MBYTES ? NW * YWARP : MBYTES));
+    static constexpr size_t o_BX = tc_al(o_Y + NW * YWARP);
     static constexpr size_t NBST = (size_t)CI * G * BP;  // floats per part of a staging buffer
     static constexpr size_t o_B = tc_al(o_BX + 2 * BXBUF);
     static constexpr size_t o_w = tc_al(o_B + 2 * 2 * NBST * 4);
@@ -80,9 +82,7 @@ struct TcPlan {
     static constexpr size_t o_R = tc_al(o_U + (size_t)NP * G * 8);
     static constexpr size_t o_dU = tc_al(o_R + (size_t)NP * G * 8);
     static constexpr size_t o_Udf = tc_al(o_dU + (size_t)NP * NS * 8);
-    static constexpr size_t o_r = tc_al(o_Udf + 2 * (size_t)NP * G * 4);
-    static constexpr size_t o_PU = tc_al(o_r + 2 * (size_t)NP * NQ * 4);
-    static constexpr size_t o_flag = tc_al(o_PU + 2 * (size_t)NP * G * 4);
+    static constexpr size_t o_flag = tc_al(o_Udf + 2 * (size_t)NP * G * 4);
     static constexpr size_t o_pidx = o_flag + NP * 4;
     // mbarriers: [0,1] table copies, [2 + 2 w + b] MMA commits of warp w; then TMEM slot, error flag
     static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);
@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     constexpr int NAR = PL::NAR, PPT = PL::PPT, NN = PL::NN, NW = PL::NW;
     constexpr int EPS = PL::EPS, KSC = PL::KSC, NT = PL::NT, RPW = PL::RPW;
     constexpr int NBST = (int)PL::NBST;
+    using CR = CondRec<D, NA>;
     extern __shared__ __align__(16) unsigned char smem[];
-    float *s_Mf = reinterpret_cast<float *>(smem + PL::o_Y);
     float *s_BX = reinterpret_cast<float *>(smem + PL::o_BX);
     float *s_Bst = reinterpret_cast<float *>(smem + PL::o_B);
     float *s_wst = reinterpret_cast<float *>(smem + PL::o_w);
@@ -113,8 +113,6 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     double *s_R = reinterpret_cast<double *>(smem + PL::o_R);
     double *s_dU = reinterpret_cast<double *>(smem + PL::o_dU);
     float *s_Uh = reinterpret_cast<float *>(smem + PL::o_Udf), *s_Ul = s_Uh + NP * G;
-    float *s_rh = reinterpret_cast<float *>(smem + PL::o_r), *s_rl = s_rh + NP * NQ;
-    float *s_puh = reinterpret_cast<float *>(smem + PL::o_PU), *s_pul = s_puh + NP * G;
     int *s_flag = reinterpret_cast<int *>(smem + PL::o_flag);
     int *s_pidx = reinterpret_cast<int *>(smem + PL::o_pidx);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + PL::o_bar);
@@ -125,7 +123,9 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     const int n = a.t.n, m = a.t.m;
     const int na = n + G;
     const int64_t count = a.count ? (int64_t)(*a.count) : a.n_points;
-    const int32_t *perm = a.perm ? a.perm + (a.offset ? *a.offset : 0) : nullptr;
+    const int64_t off = (a.perm && a.offset) ? (int64_t)(*a.offset) : 0;
+    const int32_t *perm = a.perm ? a.perm + off : nullptr;
+    float *ws = a.cond + off * CR::W;  // records of this type's points, by list position
     const int64_t n_tiles = (count + NP - 1) / NP;
     const int nch = (m + CI - 1) / CI;
     // this warp's tile: points p0 .. p0 + PPT - 1 of the CTA, its A rows, its
@@ -377,7 +377,9 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     const uint64_t adh = tc::smem_desc(tc::smem_u32(Yh), 2048, 128);
                     const uint64_t adl = tc::smem_desc(tc::smem_u32(Yl), 2048, 128);
                     const uint32_t dt = tbase + warp * NN;
-                    tc::mma_tf32(dt, adh, bdh, idesc, ks > 0 ? 1u : 0u);
+                    // a chunk's first MMA starts the accumulator fresh in the first
+                    // two chunks; later it adds onto the fold's compensation term
+                    tc::mma_tf32(dt, adh, bdh, idesc, (ks > 0 || ch >= 2) ? 1u : 0u);
                     tc::mma_tf32(dt, adh, bdl, idesc, 1u);
                     tc::mma_tf32(dt, adl, bdh, idesc, 1u);
                     tc::mma_commit(&mbar[yb]);
@@ -414,10 +416,13 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     pudf = df_add(pudf, df{WPh[(il * G + c) * PPT + pl], WPl[(il * G + c) * PPT + pl]});
             }
 
-            // fold the chunk accumulators into the running sums (TMEM); the
-            // last fold writes the augmented system of every point to shared
-            // memory.  A warp reads its lane quarter of every other tile, so it
-            // waits for the last commit of every warp.
+            // fold the chunk accumulators into the running sums (TMEM), Kahan-
+            // compensated: the compensation term is stored (negated) into the
+            // accumulator, onto which the next chunk's MMAs add, so the next
+            // fold adds (chunk sum - compensation).  The last fold writes the
+            // augmented system of every point to the workspace.  A warp reads
+            // its lane quarter of every other tile, so it waits for the last
+            // commit of every warp.
             const bool last = (ch == nch - 1);
             {
                 const uint32_t sl = gstep - 1;
@@ -437,16 +442,24 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                         if (folds > 0) tc::tmem_ld16(tbase + lanes + NW * NN + t * NN + cb * 16, vs);
                         tc::tmem_wait_ld();
                         if (folds > 0) {
+                            float cmp[16];
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) va[c] = __fadd_rn(vs[c], va[c]);
+                            for (int c = 0; c < 16; ++c) {
+                                const float tt = __fadd_rn(vs[c], va[c]);
+                                cmp[c] = __fsub_rn(va[c], __fsub_rn(tt, vs[c]));  // -(compensation)
+                                va[c] = tt;
+                            }
+                            if (!last) tc::tmem_st16(tbase + lanes + t * NN + cb * 16, cmp);
                         }
                         if (!last) {
                             tc::tmem_st16(tbase + lanes + NW * NN + t * NN + cb * 16, va);
-                        } else if (jr < NA) {
+                        } else if (jr < NA && tile * NP + p < count) {
+                            // lane jr holds column jr of M: entries (col, jr), col >= jr
+                            float *rm = ws + (tile * NP + p) * CR::W + CR::o_M;
 #pragma unroll
                             for (int c = 0; c < 16; ++c) {
                                 const int col = cb * 16 + c;
-                                if (col < NA) s_Mf[(p * NA + col) * NA + jr] = va[c];
+                                if (col < NA && col >= jr) rm[tri(col, jr)] = va[c];
                             }
                         }
                     }
@@ -460,31 +473,37 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             tc::fence_after_sync();
         }
 
-        // ---- spill the residual and Pbar_U (double-float pairs) -------------
+        // ---- workspace records of this warp's points (steps a6, a7 follow in
+        // condense_kernel): residual and V0 Pbar_U (double-float), q, R, U, status
+        const int err = *s_err;
 #pragma unroll
         for (int u = 0; u < RPW; ++u) {
             const int o = lane + 32 * u;
             if (o < PPT * NQ) {
-                const df v = df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1]));
-                s_rh[p0 * NQ + o] = v.hi;
-                s_rl[p0 * NQ + o] = v.lo;
+                const int pl = o / NQ, jj = o % NQ;
+                const int64_t li = tile * NP + p0 + pl;
+                if (li < count) {
+                    const df v = df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1]));
+                    float *rec = ws + li * CR::W;
+                    rec[CR::o_rh + jj] = v.hi;
+                    rec[CR::o_rl + jj] = v.lo;
+                    reinterpret_cast<double *>(rec + CR::o_q)[jj] = s_qd[(p0 + pl) * QP + jj];
+                }
             }
         }
         if (lane < PPT * G) {
-            s_puh[p0 * G + lane] = pudf.hi;
-            s_pul[p0 * G + lane] = pudf.lo;
+            const int pl = lane / G, c = lane % G;
+            const int64_t li = tile * NP + p0 + pl;
+            if (li < count) {
+                float *rec = ws + li * CR::W;
+                rec[CR::o_ph + c] = pudf.hi;
+                rec[CR::o_pl + c] = pudf.lo;
+                reinterpret_cast<double *>(rec + CR::o_R)[c] = s_R[(p0 + pl) * G + c];
+                reinterpret_cast<double *>(rec + CR::o_U)[c] = s_U[(p0 + pl) * G + c];
+                if (c == 0) *reinterpret_cast<int *>(rec + CR::o_flag) = err ? ST_TIMEOUT : s_flag[p0 + pl];
+            }
         }
         __syncthreads();
-        // ---- a6, a7: condensation and outputs, one warp per point -----------
-        for (int p = warp; p < NP; p += NW) {
-            const int gp = s_pidx[p];
-            if (gp < 0) continue;
-            condense_out_regs_mix<D, NA, NQ>(a, s_Mf + p * NA * NA, s_rh + p * NQ, s_rl + p * NQ, s_puh + p * G,
-                                             s_pul + p * G, gp, s_flag[p], n, s_qd + p * QP, s_R + p * G,
-                                             s_U + p * G, (float)(1.0 / a.V0), lane);
-        }
-        __syncthreads();
-        if (*s_err && tid < NP && s_pidx[tid] >= 0) a.status[s_pidx[tid]] = ST_TIMEOUT;
     }
     tc::fence_before_sync();
     __syncthreads();

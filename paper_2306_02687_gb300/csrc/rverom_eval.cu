@@ -93,6 +93,16 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out) {
     return k < max_out ? k : max_out;
 }
 
+// workspace record size (floats) of the tensor-core configuration serving n
+// modes (0 if none does)
+int tc_record_words(int dim, int n) {
+    if (dim != 2) return 0;
+    if (n <= 12) return CondRec<2, 16>::W;
+    if (n <= 16) return CondRec<2, 20>::W;
+    if (n <= 24) return CondRec<2, 28>::W;
+    return 0;
+}
+
 // float32 value rounded to TF32 (10 fraction bits), ties away from zero
 static float tf32_rna(float x) {
     uint32_t u;
@@ -230,6 +240,8 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
             return RVEROM_ERR_CUDA;
         }
         if (d.n_modes > h->nmax) h->nmax = d.n_modes;
+        const int cw = tc_record_words(dim, d.n_modes);
+        if (cw > h->cond_words) h->cond_words = cw;
     }
     if (cudaMalloc(&h->bucket_small, 4 * (RVEROM_MAX_TYPES + 1) * sizeof(int32_t)) != cudaSuccess) {
         rve_rom_destroy(h);
@@ -255,6 +267,7 @@ extern "C" int rve_rom_destroy(rverom_t h) {
     cudaFree(h->bucket_small);
     cudaFree(h->perm);
     cudaFree(h->partials);
+    cudaFree(h->cond);
     delete h;
     return RVEROM_OK;
 }
@@ -312,6 +325,17 @@ extern "C" int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *t
     cudaStream_t st = (cudaStream_t)stream;
     int rc = prepare_buckets(h, n_points, type, status, rnorm, st);
     if (rc != RVEROM_OK) return rc;
+    if (precision == RVEROM_MIXED && h->cond_words > 0 && h->cond_cap < n_points * h->cond_words) {
+        // workspace of the tensor-core form (grown here, outside any stream capture
+        // when the first call at this batch size precedes the capture)
+        cudaStreamSynchronize(st);
+        cudaFree(h->cond);
+        h->cond = nullptr;
+        h->cond_cap = 0;
+        if (cudaMalloc(&h->cond, (size_t)n_points * h->cond_words * sizeof(float)) != cudaSuccess)
+            return RVEROM_ERR_CUDA;
+        h->cond_cap = n_points * h->cond_words;
+    }
     for (int t = 0; t < h->n_types; ++t) {
         if (!type && t > 0) break;
         EvalArgs a;
@@ -331,6 +355,7 @@ extern "C" int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *t
         a.gP = nullptr;
         a.gF = nullptr;
         a.partials = nullptr;
+        a.cond = precision == RVEROM_MIXED ? h->cond : nullptr;
         if (type) {
             a.perm = h->perm;
             a.count = h->bucket_small + t;
@@ -409,6 +434,13 @@ extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample,
     }
     double *Fbar = buf, *q = Fbar + n * g, *s = q + n * h->nmax, *S = s + n * h->nmax, *U = S + n * h->nmax * ns;
     double *Pbar = U + n * ns, *dPdF = Pbar + n * g, *rnorm = dPdF + n * g * g;
+    float *cond = nullptr;
+    if (precision == RVEROM_MIXED && h->cond_words > 0 &&
+        cudaMalloc(&cond, (size_t)n * h->cond_words * sizeof(float)) != cudaSuccess) {
+        cudaFree(buf);
+        cudaFree(status);
+        return RVEROM_ERR_CUDA;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -434,6 +466,7 @@ extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample,
             a.dPdF = dPdF;
             a.rnorm = rnorm;
             a.status = status;
+            a.cond = cond;
             float tbest = 1e30f;
             for (int rep = 0; rep < 3 && rc == RVEROM_OK; ++rep) {
                 k_tune_inputs<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(
@@ -461,5 +494,6 @@ extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample,
     cudaStreamSynchronize(st);
     cudaFree(buf);
     cudaFree(status);
+    cudaFree(cond);
     return rc;
 }

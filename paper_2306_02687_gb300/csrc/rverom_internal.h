@@ -22,6 +22,9 @@ struct rverom_s {
     double *partials = nullptr;       // per-CTA partial sums of the adjoint
     int64_t partials_cap = 0;
     int choice[RVEROM_MAX_TYPES][2] = {};  // forward kernel candidate per type and precision
+    float *cond = nullptr;            // per-point workspace records of the tensor-core form
+    int64_t cond_cap = 0;             // in floats
+    int cond_words = 0;               // record size (floats) of the largest tensor-core configuration
 };
 
 namespace rverom {
@@ -67,23 +70,38 @@ cudaError_t launch_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaStrea
     return cudaGetLastError();
 }
 
-// Tensor-core mixed-precision forward kernel <D, NA, NP, CI>: one CTA per
-// SM (its shared memory and TMEM allocation fill the SM).
+// Tensor-core mixed-precision forward kernel <D, NA, NP, CI> (one CTA per
+// SM: its shared memory and TMEM allocation fill the SM), followed by the
+// per-thread condensation of its workspace records.
 template <int D, int NA, int NP, int CI>
 cudaError_t launch_tc(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
     using PL = TcPlan<D, NA, NP, CI>;
-    if (!a.t.Bimg || a.t.img_nn != PL::NN) return cudaErrorInvalidValue;
+    constexpr int CT = 32, TPP = 4;
+    using CP = CondPlan<D, NA, CT, TPP>;
+    if (!a.t.Bimg || a.t.img_nn != PL::NN || !a.cond) return cudaErrorInvalidValue;
     auto kern = eval_tc_kernel<D, NA, NP, CI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
     if (e != cudaSuccess) return e;
+    auto ckern = condense_kernel<D, NA, CT, TPP>;
+    e = cudaFuncSetAttribute(ckern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP::bytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ckern, CT * TPP, CP::bytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     int64_t tiles = (max_points + NP - 1) / NP;
     int64_t grid = n_sm;
     if (tiles < grid) grid = tiles;
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;
     kern<<<(unsigned)grid, PL::NT, PL::bytes, st>>>(a);
+    int64_t cgrid = (max_points + CT - 1) / CT, cmax = (int64_t)n_sm * occ;
+    if (cgrid > cmax) cgrid = cmax;
+    if (cgrid < 1) cgrid = 1;
+    ckern<<<(unsigned)cgrid, CT * TPP, CP::bytes, st>>>(a);
     return cudaGetLastError();
 }
+int tc_record_words(int dim, int n);
 
 // Tile configuration per (dimension, n~ bucket, precision).
 template <bool ADJ>
