@@ -52,9 +52,11 @@ WORKLOADS = {
 }
 
 # DRAM traffic per launch of the evaluation kernel from one ncu capture of
-# this workload (profiles/eval_kernel_c2_*_full.md); reported only for that
-# workload and form, and to be refreshed whenever the kernel changes.
-PROFILED_TRAFFIC = {('c2', 'mixed'): 17014528, ('c2', 'fp64'): 17142784}
+# this workload (profiles/eval_tc_kernel_c2_full.md for the mixed form, whose
+# autotuned kernel is the tensor-core one; profiles/eval_kernel_c2_fp64_full.md);
+# reported only for that workload and form, and to be refreshed whenever the
+# kernel changes.
+PROFILED_TRAFFIC = {('c2', 'mixed'): 17259520, ('c2', 'fp64'): 17142784}
 
 # algorithmic work per evaluation (FP64 FLOP of kinematics + residual + law,
 # symmetric-half tangent contraction FLOP), per ROM type
@@ -367,6 +369,7 @@ def main():
         return 0
 
     # roofline of the dominant kernel (the batched RVE evaluation)
+    kinfo = [rv.rve_rom_kernel_info(h, t, args.precision) for t in range(len(roms))]
     n_per_type = np.bincount(types_np, minlength=len(roms))
     w64 = sum(c * work_per_eval(r)[0] for c, r in zip(n_per_type, roms))
     w32 = sum(c * work_per_eval(r)[1] for c, r in zip(n_per_type, roms))
@@ -383,7 +386,8 @@ def main():
         src = 'nominal: 152 SMs x 128 FFMA/clk x 2 FLOP x 2.07 GHz (measured 74.1 TFLOP/s in an FFMA probe)'
     roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
                 "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get((args.workload, args.precision)),
-                "kernel": "rverom::eval_kernel (autotuned configuration)", "binding": unitname,
+                "kernel": "; ".join(nm for nm, _ in kinfo) + (" (selected)" if args.candidate >= 0 else " (autotuned)"),
+                "binding": unitname,
                 "peak_source": src, "kernel_ms": ms_kern,
                 "algorithmic_flop_per_eval": {"fp64_accurate": w64 / n, "fp32": w32 / n}}
 
@@ -399,9 +403,9 @@ def main():
                "sample": "%d evaluations (cycling over %d of the %d points) in %.1f s, float64 NumPy oracle, one thread"
                          % (cnt, len(sel), n, el)}
 
-    launches = 4 * args.steps  # gradient, evaluation, assembly, norms (single type)
-    if len(roms) > 1:
-        launches = (3 + 3 + len(roms)) * args.steps
+    # our kernels per step: gradient, (bucketing: 3 with several types),
+    # the evaluation kernels of every type, assembly, norms
+    launches = (3 + (3 if len(roms) > 1 else 0) + sum(nl for _, nl in kinfo)) * args.steps
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

@@ -137,6 +137,17 @@ int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample, float *ms_
 int rve_rom_select_kernel(rverom_t h, int32_t type, int32_t precision, int32_t candidate,
                           int32_t *n_candidates);
 
+/* Name and kernel launches of a forward candidate of one type and precision
+ * (candidate < 0: the one rve_rom_eval_batch currently uses, i.e. the
+ * autotuner's or rve_rom_select_kernel's pick, else 0).  `name` receives a
+ * NUL-terminated, possibly truncated description in a caller buffer of `len`
+ * bytes (may be NULL); `launches` (may be NULL) the number of kernels the
+ * candidate launches for this type per rve_rom_eval_batch call.  Host only;
+ * RVEROM_ERR_ARG for a bad handle, type, precision or candidate.  (A query
+ * of this library's dispatch: the paper has no counterpart.) */
+int rve_rom_kernel_info(rverom_t h, int32_t type, int32_t precision, int32_t candidate, char *name, int32_t len,
+                        int32_t *launches);
+
 /* Implicit-function adjoint at converged states (r(q*) = 0): for cotangents
  * gPbar on Pbar,
  *   gFbar = dPdF^T gPbar      (the condensed consistent tangent)

@@ -30,6 +30,7 @@ SIGNATURES = {
     'rve_rom_nmax': (c_int, [c_vp, P(c_int)]),
     'rve_rom_autotune': (c_int, [c_vp, c_int, c_i64, P(ctypes.c_float), c_vp]),
     'rve_rom_select_kernel': (c_int, [c_vp, c_int, c_int, c_int, P(c_int)]),
+    'rve_rom_kernel_info': (c_int, [c_vp, c_int, c_int, c_int, ctypes.c_char_p, c_int, P(c_int)]),
     'rve_rom_eval_batch': (c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                    c_vp, c_vp, c_int, c_vp]),
     'rve_rom_adjoint': (c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -148,6 +148,16 @@ def rve_rom_select_kernel(h, type_id, precision, candidate=-1):
     return nc.value
 
 
+def rve_rom_kernel_info(h, type_id, precision, candidate=-1):
+    """(name, kernel launches per call) of a forward candidate; candidate < 0
+    is the one currently used for this type and precision."""
+    buf = ctypes.create_string_buffer(128)
+    nl = ctypes.c_int32()
+    _native.check(_native.lib().rve_rom_kernel_info(h.ptr, int(type_id), _PREC[precision], int(candidate), buf,
+                                                    len(buf), ctypes.byref(nl)), 'rve_rom_kernel_info')
+    return buf.value.decode(), nl.value
+
+
 def rve_rom_eval_batch(h, Fbar, q, s, S, Uprev, Pbar, dPdF, rnorm, status, type=None,
                        precision='mixed', stream=None):
     n = Fbar.shape[0]

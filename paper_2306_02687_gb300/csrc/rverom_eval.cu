@@ -56,40 +56,52 @@ bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) |
 #define RV_SYM(D, NA, TA, NP, CI, KT) &launch_cfg<D, NA, TA, TA, NP, CI, KT, false, true>
 #define RV_TC(D, NA, NP, CI) &launch_tc<D, NA, NP, CI>
 
-int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out) {
+int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, CandInfo *info) {
     LaunchFn c[4] = {};
+    CandInfo ci[4] = {};
     int k = 0;
+    auto add = [&](LaunchFn f, const char *name, int launches) {
+        c[k] = f;
+        ci[k] = CandInfo{name, launches};
+        ++k;
+    };
     if (dim == 2 && mixed) {
         if (n <= 12) {
-            c[k++] = RV_SYM(2, 16, 4, 24, 10, float);
-            c[k++] = RV_FUSED(2, 16, 4, 4, 16, 16, float);
-            c[k++] = RV_WS(2, 16, 4, 4, 8, 16);
-            c[k++] = RV_TC(2, 16, 64, 4);
+            add(RV_SYM(2, 16, 4, 24, 10, float), "simt-symmetric <2,16> 24 points x 10 ECM", 1);
+            add(RV_FUSED(2, 16, 4, 4, 16, 16, float), "simt-fused <2,16> 16 points x 16 ECM", 1);
+            add(RV_WS(2, 16, 4, 4, 8, 16), "simt-warp-specialized <2,16> 8 points x 16 ECM", 1);
+            add(RV_TC(2, 16, 64, 4), "tcgen05-tf32x3 <2,16> 64 points x 4 ECM + per-thread condensation", 2);
         } else if (n <= 16) {
-            c[k++] = RV_SYM(2, 20, 5, 24, 10, float);
-            c[k++] = RV_FUSED(2, 20, 5, 5, 16, 16, float);
-            c[k++] = RV_WS(2, 20, 5, 5, 8, 16);
-            c[k++] = RV_TC(2, 20, 32, 8);
+            add(RV_SYM(2, 20, 5, 24, 10, float), "simt-symmetric <2,20> 24 points x 10 ECM", 1);
+            add(RV_FUSED(2, 20, 5, 5, 16, 16, float), "simt-fused <2,20> 16 points x 16 ECM", 1);
+            add(RV_WS(2, 20, 5, 5, 8, 16), "simt-warp-specialized <2,20> 8 points x 16 ECM", 1);
+            add(RV_TC(2, 20, 32, 8), "tcgen05-tf32x3 <2,20> 32 points x 8 ECM + per-thread condensation", 2);
         } else if (n <= 24) {
-            c[k++] = RV_SYM(2, 28, 7, 24, 10, float);
-            c[k++] = RV_FUSED(2, 28, 7, 7, 16, 16, float);
-            c[k++] = RV_WS(2, 28, 7, 7, 8, 16);
-            c[k++] = RV_TC(2, 28, 32, 8);
+            add(RV_SYM(2, 28, 7, 24, 10, float), "simt-symmetric <2,28> 24 points x 10 ECM", 1);
+            add(RV_FUSED(2, 28, 7, 7, 16, 16, float), "simt-fused <2,28> 16 points x 16 ECM", 1);
+            add(RV_WS(2, 28, 7, 7, 8, 16), "simt-warp-specialized <2,28> 8 points x 16 ECM", 1);
+            add(RV_TC(2, 28, 32, 8), "tcgen05-tf32x3 <2,28> 32 points x 8 ECM + per-thread condensation", 2);
         } else if (n <= 32) {
-            c[k++] = RV_FUSED(2, 36, 9, 9, 16, 8, float);
+            add(RV_FUSED(2, 36, 9, 9, 16, 8, float), "simt-fused <2,36> 16 points x 8 ECM", 1);
         } else if (n <= 64) {
-            c[k++] = RV_FUSED(2, 72, 9, 9, 4, 8, float);
+            add(RV_FUSED(2, 72, 9, 9, 4, 8, float), "simt-fused <2,72> 4 points x 8 ECM", 1);
         }
     } else if (dim == 2) {
-        if (n <= 12) c[k++] = RV_FUSED(2, 16, 4, 4, 16, 8, double);
-        else if (n <= 16) c[k++] = RV_FUSED(2, 20, 5, 5, 16, 8, double);
-        else if (n <= 24) c[k++] = RV_FUSED(2, 28, 7, 7, 8, 8, double);
-        else if (n <= 32) c[k++] = RV_FUSED(2, 36, 9, 9, 8, 8, double);
-        else if (n <= 64) c[k++] = RV_FUSED(2, 72, 9, 9, 2, 8, double);
+        if (n <= 12) add(RV_FUSED(2, 16, 4, 4, 16, 8, double), "fp64-fused <2,16> 16 points x 8 ECM", 1);
+        else if (n <= 16) add(RV_FUSED(2, 20, 5, 5, 16, 8, double), "fp64-fused <2,20> 16 points x 8 ECM", 1);
+        else if (n <= 24) add(RV_FUSED(2, 28, 7, 7, 8, 8, double), "fp64-fused <2,28> 8 points x 8 ECM", 1);
+        else if (n <= 32) add(RV_FUSED(2, 36, 9, 9, 8, 8, double), "fp64-fused <2,36> 8 points x 8 ECM", 1);
+        else if (n <= 64) add(RV_FUSED(2, 72, 9, 9, 2, 8, double), "fp64-fused <2,72> 2 points x 8 ECM", 1);
     } else if (dim == 3) {
-        if (n <= 47) c[k++] = mixed ? RV_FUSED(3, 56, 7, 7, 4, 8, float) : RV_FUSED(3, 56, 7, 7, 2, 4, double);
+        if (n <= 47) {
+            if (mixed) add(RV_FUSED(3, 56, 7, 7, 4, 8, float), "simt-fused <3,56> 4 points x 8 ECM", 1);
+            else add(RV_FUSED(3, 56, 7, 7, 2, 4, double), "fp64-fused <3,56> 2 points x 4 ECM", 1);
+        }
     }
-    for (int i = 0; i < k && i < max_out; ++i) out[i] = c[i];
+    for (int i = 0; i < k && i < max_out; ++i) {
+        out[i] = c[i];
+        if (info) info[i] = ci[i];
+    }
     return k < max_out ? k : max_out;
 }
 
@@ -415,6 +427,24 @@ extern "C" int rve_rom_select_kernel(rverom_t h, int32_t type, int32_t precision
     if (candidate < 0) return RVEROM_OK;  // query only
     if (candidate >= nc) return RVEROM_ERR_ARG;
     h->choice[type][precision == RVEROM_MIXED ? 1 : 0] = candidate;
+    return RVEROM_OK;
+}
+
+extern "C" int rve_rom_kernel_info(rverom_t h, int32_t type, int32_t precision, int32_t candidate, char *name,
+                                   int32_t len, int32_t *launches) {
+    if (!h || type < 0 || type >= h->n_types || (precision != RVEROM_FP64 && precision != RVEROM_MIXED))
+        return RVEROM_ERR_ARG;
+    LaunchFn cand[8];
+    CandInfo info[8];
+    const int nc = forward_candidates(h->dim, h->types[type].n, precision == RVEROM_MIXED, cand, 8, info);
+    const int pick = h->choice[type][precision == RVEROM_MIXED ? 1 : 0];
+    const int c = candidate < 0 ? ((pick >= 0 && pick < nc) ? pick : 0) : candidate;
+    if (c >= nc) return RVEROM_ERR_ARG;
+    if (name && len > 0) {
+        std::strncpy(name, info[c].name, (size_t)len - 1);
+        name[len - 1] = '\0';
+    }
+    if (launches) *launches = info[c].launches;
     return RVEROM_OK;
 }
 

@@ -140,7 +140,12 @@ int prepare_buckets(rverom_t h, int64_t n, const int32_t *type, int32_t *status,
                     cudaStream_t st);
 
 // Candidate forward kernels (tile configurations) of an RVE type; entry 0 is
-// the default before autotuning.  Returns the number of candidates.
+// the default before autotuning.  Returns the number of candidates; `info`
+// (optional) receives each candidate's name and kernel launches per type.
 using LaunchFn = cudaError_t (*)(const EvalArgs &, int, int64_t, cudaStream_t, int *);
-int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out);
+struct CandInfo {
+    const char *name;
+    int launches;
+};
+int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, CandInfo *info = nullptr);
 }  // namespace rverom

@@ -308,6 +308,11 @@ def test_every_tile_configuration_matches_oracle(names):
             compare(run_gpu(h, F, q, s, S, U, precision, types=types), outs, h.nmax, tol)
         ms = rv.rve_rom_autotune(h, precision, n_sample=2048)
         assert np.all(ms[:, 0] > 0)
+        for t in range(len(names)):
+            # the candidate in use is the fastest one, and every candidate names itself
+            infos = [rv.rve_rom_kernel_info(h, t, precision, c) for c in range(counts[t])]
+            assert all(nm and nl in (1, 2) for nm, nl in infos)
+            assert rv.rve_rom_kernel_info(h, t, precision) == infos[int(np.argmin(ms[t, :counts[t]]))]
         compare(run_gpu(h, F, q, s, S, U, precision, types=types), outs, h.nmax, tol)
 
 
