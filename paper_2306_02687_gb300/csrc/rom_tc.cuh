@@ -436,29 +436,54 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     const int row = t * 128 + qd * 32 + lane;
                     const int p = row / NAR, jr = row % NAR;
 #pragma unroll
-                    for (int cb = 0; cb < NN / 16; ++cb) {
-                        float va[16], vs[16];
-                        tc::tmem_ld16(tbase + lanes + t * NN + cb * 16, va);
-                        if (folds > 0) tc::tmem_ld16(tbase + lanes + NW * NN + t * NN + cb * 16, vs);
+                    for (int cb = 0; cb < NN / 32; ++cb) {
+                        float va[32], vs[32];
+                        tc::tmem_ld32(tbase + lanes + t * NN + cb * 32, va);
+                        if (folds > 0) tc::tmem_ld32(tbase + lanes + NW * NN + t * NN + cb * 32, vs);
                         tc::tmem_wait_ld();
                         if (folds > 0) {
-                            float cmp[16];
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) {
+                            for (int c = 0; c < 32; ++c) {
                                 const float tt = __fadd_rn(vs[c], va[c]);
-                                cmp[c] = __fsub_rn(va[c], __fsub_rn(tt, vs[c]));  // -(compensation)
+                                vs[c] = __fsub_rn(va[c], __fsub_rn(tt, vs[c]));  // -(compensation)
                                 va[c] = tt;
                             }
-                            if (!last) tc::tmem_st16(tbase + lanes + t * NN + cb * 16, cmp);
+                            if (!last) tc::tmem_st32(tbase + lanes + t * NN + cb * 32, vs);
                         }
                         if (!last) {
-                            tc::tmem_st16(tbase + lanes + NW * NN + t * NN + cb * 16, va);
+                            tc::tmem_st32(tbase + lanes + NW * NN + t * NN + cb * 32, va);
                         } else if (jr < NA && tile * NP + p < count) {
                             // lane jr holds column jr of M: entries (col, jr), col >= jr
                             float *rm = ws + (tile * NP + p) * CR::W + CR::o_M;
 #pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                const int col = cb * 32 + c;
+                                if (col < NA && col >= jr) rm[tri(col, jr)] = va[c];
+                            }
+                        }
+                    }
+                    if (NN % 32) {
+                        constexpr int cb = NN / 32;
+                        float va[16], vs[16];
+                        tc::tmem_ld16(tbase + lanes + t * NN + cb * 32, va);
+                        if (folds > 0) tc::tmem_ld16(tbase + lanes + NW * NN + t * NN + cb * 32, vs);
+                        tc::tmem_wait_ld();
+                        if (folds > 0) {
+#pragma unroll
                             for (int c = 0; c < 16; ++c) {
-                                const int col = cb * 16 + c;
+                                const float tt = __fadd_rn(vs[c], va[c]);
+                                vs[c] = __fsub_rn(va[c], __fsub_rn(tt, vs[c]));
+                                va[c] = tt;
+                            }
+                            if (!last) tc::tmem_st16(tbase + lanes + t * NN + cb * 32, vs);
+                        }
+                        if (!last) {
+                            tc::tmem_st16(tbase + lanes + NW * NN + t * NN + cb * 32, va);
+                        } else if (jr < NA && tile * NP + p < count) {
+                            float *rm = ws + (tile * NP + p) * CR::W + CR::o_M;
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                const int col = cb * 32 + c;
                                 if (col < NA && col >= jr) rm[tri(col, jr)] = va[c];
                             }
                         }
