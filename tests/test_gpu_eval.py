@@ -160,7 +160,19 @@ def test_converged_stress_matches_oracle(c1, precision):
         assert rel(C[a], o['dPdF']) <= (1e-10 if precision == 'fp64' else 1e-5)
 
 
-def test_status_codes_and_empty_batch(c1):
+def each_candidate(h, precision):
+    """Select every compiled forward candidate of type 0 in turn."""
+    nc = rv.rve_rom_select_kernel(h, 0, precision)
+    for c in range(nc):
+        rv.rve_rom_select_kernel(h, 0, precision, c)
+        yield c
+    rv.rve_rom_select_kernel(h, 0, precision, 0)
+
+
+@pytest.mark.parametrize('precision', ['fp64', 'mixed'])
+def test_status_codes_and_empty_batch(c1, precision):
+    # every candidate (SIMT and tensor-core forms) reports the same statuses,
+    # NaN outputs for failed points and leaves their micro state untouched
     h, oroms = c1
     n = 5
     F = syn.fbar_batch(syn.SEED_BASE + 15, 2, n, 0.1, 0.3)
@@ -168,15 +180,18 @@ def test_status_codes_and_empty_batch(c1):
     F[3, 0, 0] = np.nan                                  # non-finite input
     q, s, S, U = (np.zeros((n, h.nmax)), np.zeros((n, h.nmax)), np.zeros((n, h.nmax, 3)),
                   np.tile([1.0, 1.0, 0.0], (n, 1)))
-    g = run_gpu(h, F, q, s, S, U, 'fp64')
-    assert list(g['status']) == [0, 1, 0, 3, 0]
-    assert np.all(np.isnan(g['Pbar'][[1, 3]]))
-    # micro det F <= 0: a huge fluctuation amplitude folds some ECM point
     q2 = q.copy()
     q2[0] = 50.0
-    g2 = run_gpu(h, F[[0]], q2[[0]], s[[0]], S[[0]], U[[0]], 'fp64')
     o2 = reduced.eval_point(oroms[0], F[0], q2[0], s[0], S[0], U[0])
-    assert g2['status'][0] == o2['status'] == 1
+    for _ in each_candidate(h, precision):
+        g = run_gpu(h, F, q, s, S, U, precision)
+        assert list(g['status']) == [0, 1, 0, 3, 0]
+        assert np.all(np.isnan(g['Pbar'][[1, 3]])) and np.all(np.isnan(g['dPdF'][[1, 3]]))
+        assert np.all(np.isfinite(g['Pbar'][[0, 2, 4]]))
+        # micro det F <= 0: a huge fluctuation amplitude folds some ECM point
+        g2 = run_gpu(h, F[[0]], q2[[0]], s[[0]], S[[0]], U[[0]], precision)
+        assert g2['status'][0] == o2['status'] == 1
+        assert np.array_equal(g2['q'][0], q2[0]) and np.array_equal(g2['Uprev'][0], U[0])
     # empty batch is a no-op
     z = torch.zeros(0, 4, dtype=torch.float64, device='cuda')
     qz, sz, Sz, Uz = h.zero_state(0)
@@ -184,7 +199,8 @@ def test_status_codes_and_empty_batch(c1):
     rv.rve_rom_eval_batch(h, z, qz, sz, Sz, Uz, Pz, dz, rz, stz)
 
 
-def test_nonspd_reduced_stiffness():
+@pytest.mark.parametrize('precision', ['fp64', 'mixed'])
+def test_nonspd_reduced_stiffness(precision):
     h, oroms = _handle(['c1'])
     mod = oroms[0].moduli.copy()
     mod[:, 0] = -0.3                                     # negative shear modulus
@@ -193,11 +209,13 @@ def test_nonspd_reduced_stiffness():
     F = syn.fbar_batch(syn.SEED_BASE + 16, 2, n, 0.05, 0.0)
     q, s, S, U = (np.zeros((n, h.nmax)), np.zeros((n, h.nmax)), np.zeros((n, h.nmax, 3)),
                   np.tile([1.0, 1.0, 0.0], (n, 1)))
-    g = run_gpu(h, F, q, s, S, U, 'fp64')
     r = oroms[0].with_moduli(mod)
-    for a in range(n):
-        o = reduced.eval_point(r, F[a], q[a], s[a], S[a], U[a])
-        assert g['status'][a] == o['status'] == 2
+    outs = [reduced.eval_point(r, F[a], q[a], s[a], S[a], U[a]) for a in range(n)]
+    for _ in each_candidate(h, precision):
+        g = run_gpu(h, F, q, s, S, U, precision)
+        for a in range(n):
+            assert g['status'][a] == outs[a]['status'] == 2
+        assert np.all(np.isnan(g['Pbar']))
 
 
 def test_full_size_2d_sampled():
