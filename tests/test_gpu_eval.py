@@ -376,3 +376,24 @@ def test_tensor_core_kernel_many_tiles(name):
     assert np.array_equal(g['q'], ref['q']) and np.array_equal(g['Uprev'], ref['Uprev'])
     compare({k: v[idx] for k, v in g.items()}, oracle_batch(oroms, F[idx], q[idx], s[idx], S[idx], U[idx]),
             h.nmax, TOL_MIXED)
+
+
+@pytest.mark.parametrize('name,n_keep', [('c1', 10), ('c2', 20), ('c2', 17)])
+def test_truncated_rom_every_candidate(name, n_keep):
+    # a ROM with fewer modes than its tile configuration holds (padding rows
+    # and columns of the augmented system, and of the tensor-core A operand
+    # and B-operand image): the first n_keep modes of a stored ROM form a
+    # valid ROM, evaluated by every candidate of both forms against the oracle
+    import os
+    if not os.path.exists(rom_path(name)):
+        pytest.skip('ROM file not generated')
+    full = rv.load_rom_file(rom_path(name))
+    rom = dict(full, B=np.ascontiguousarray(full['B'][:, :, :n_keep]))
+    h = rv.rve_rom_create(2, [rom], rom['V0'])
+    orom = reduced.Rom(rom['B'], rom['w'], rom['phase'], rom['moduli'], rom['V0'])
+    n = 9
+    F, q, s, S, U = mid_newton_inputs(orom, n, syn.SEED_BASE + 80 + n_keep)
+    outs = oracle_batch([orom], F, q, s, S, U)
+    for precision, tol in (('fp64', TOL_FP64), ('mixed', TOL_MIXED)):
+        for _ in each_candidate(h, precision):
+            compare(run_gpu(h, F, q, s, S, U, precision), outs, h.nmax, tol)
