@@ -23,8 +23,9 @@
 // the lanes of a warp touch consecutive banks), so every step of the
 // factorization is one conflict-free shared-memory access per point; CTA
 // barriers separate the column scaling and the trailing update of a pivot
-// step.  Four warps per 32 points keep several warps per scheduler busy
-// although each point's matrix occupies 1.8 KB of shared memory.
+// step.  Eight warps per 32 points (TPP = 8; 4 and 16 measured slower on
+// the 24-mode ROM) keep several warps per scheduler busy although each
+// point's matrix occupies 1.8 KB of shared memory.
 #pragma once
 
 #include "rom_core.cuh"

@@ -76,7 +76,7 @@ cudaError_t launch_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaStrea
 template <int D, int NA, int NP, int CI>
 cudaError_t launch_tc(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
     using PL = TcPlan<D, NA, NP, CI>;
-    constexpr int CT = 32, TPP = 4;
+    constexpr int CT = 32, TPP = 8;
     using CP = CondPlan<D, NA, CT, TPP>;
     if (!a.t.Bimg || a.t.img_nn != PL::NN || !a.cond) return cudaErrorInvalidValue;
     auto kern = eval_tc_kernel<D, NA, NP, CI>;
