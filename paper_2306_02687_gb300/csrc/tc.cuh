@@ -180,13 +180,17 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 }
 
 // ---- TF32 split -------------------------------------------------------------
-// x = hi + lo exactly; hi is x rounded to the nearest TF32 value (10 fraction
-// bits; ties away from zero) by two integer ops on the bit pattern, lo the
-// remainder (|lo| <= 2^-11 |x|, either sign: the splitting errors of many
-// products do not add up with a bias; the MMA reads lo truncated to TF32, so
-// hi + lo reaches x to about 2^-22 relative).  Finite x only.
+// nearest TF32 value (10 fraction bits; ties away from zero) by two integer
+// ops on the bit pattern; finite x only
+__device__ __forceinline__ float round_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+// x = hi + lo exactly; hi is x rounded to TF32, lo the remainder (|lo| <=
+// 2^-11 |x|, either sign: the splitting errors of many products do not add up
+// with a bias; the MMA reads lo truncated to TF32, so hi + lo reaches x to
+// about 2^-21 relative).
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-    hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+    hi = round_tf32(x);
     lo = __fsub_rn(x, hi);
 }
 
