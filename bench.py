@@ -390,6 +390,22 @@ def main():
                 "binding": unitname,
                 "peak_source": src, "kernel_ms": ms_kern,
                 "algorithmic_flop_per_eval": {"fp64_accurate": w64 / n, "fp32": w32 / n}}
+    # the other two units, for reference: the tensor pipe (the contraction's
+    # algorithmic FLOPs against the TF32 peak: measured bf16 x the nominal
+    # TF32 / BF16 ratio 1.1 / 2.25) and HBM (the profiled DRAM bytes per launch)
+    try:
+        peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
+        tf32_peak, hbm_peak, psrc = peaks['bf16_tflops'] * 1.1 / 2.25, peaks['hbm_gbs'], 'measured'
+    except (OSError, KeyError, ValueError):
+        tf32_peak, hbm_peak, psrc = 1900.0 * 1.1 / 2.25, 6800.0, 'fallback'
+    tensor_ach = w32 / (ms_kern * 1e-3) / 1e12
+    roofline["other_units"] = {
+        "tensor": {"achieved": tensor_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tensor_ach / tf32_peak,
+                   "peak_source": psrc + " bf16 x 1.1/2.25 (TF32)",
+                   "note": "algorithmic contraction FLOPs; the tensor-core form issues three TF32 passes"},
+        "hbm": None if roofline["traffic"] is None else {
+            "achieved": roofline["traffic"] / (ms_kern * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": roofline["traffic"] / (ms_kern * 1e-3) / 1e9 / hbm_peak, "peak_source": psrc}}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

@@ -127,8 +127,8 @@ static float tf32_rna(float x) {
 
 // B operand image of [B_i | I] for the tensor-core kernels (planar types):
 // per k-step of 8 (k = i * g + c, two ECM points), the TF32 leading part and
-// the trailing part (the remainder, rounded to TF32 as well), each
-// [nn/8][2][8][4] (core matrices of 8 columns x 4 k).
+// the trailing part (the float32 remainder, read by the MMA truncated to
+// TF32), each [nn/8][2][8][4] (core matrices of 8 columns x 4 k).
 // k-steps past m*g are zero; the count is padded to a multiple of 16.
 static std::vector<float> tc_table_image(const rverom_type_desc &d, int g, int nn) {
     const int n = d.n_modes, m = d.n_ecm;
@@ -139,7 +139,7 @@ static std::vector<float> tc_table_image(const rverom_type_desc &d, int g, int n
         for (int col = 0; col < n + g; ++col) {
             const double v = col < n ? d.B[((size_t)i * g + c) * n + col] : (col - n == c ? 1.0 : 0.0);
             const float hi = tf32_rna((float)v);
-            const float lo = tf32_rna((float)(v - (double)hi));
+            const float lo = (float)(v - (double)hi);
             const size_t idx = (size_t)s * 2 * nn * 8 + (col / 8) * 64 + kg * 32 + (col % 8) * 4 + e;
             img[idx] = hi;
             img[idx + (size_t)nn * 8] = lo;
