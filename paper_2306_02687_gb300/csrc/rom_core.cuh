@@ -1054,6 +1054,10 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
     constexpr int TPP = PL::TPP, NT = PL::NT, KC = PL::KC, RPT = PL::RPT;
     constexpr int NTB = NA / TB;
     constexpr int NAP = PL::NAP;
+    // one task over several lanes in the pointwise phase of the mixed
+    // configurations whose (point, ECM point) tasks fill at most half the CTA
+    // (the wide ones: few points per CTA)
+    constexpr bool SPLIT = MIX && !ADJ && 2 * NP * CI <= NT;
     using XT = KT;  // precision of K^-1 K_qF (feeds S and the adjoint's z)
     extern __shared__ __align__(16) unsigned char smem[];
     double *sd = reinterpret_cast<double *>(smem);
@@ -1274,7 +1278,84 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
             }
             __syncthreads();
 
-            // pointwise: F_i, law, w P_i, Y_i = w A_i [B_i | I]
+            // pointwise: F_i, law, w P_i, Y_i = w A_i [B_i | I].
+            // Wide mixed configurations (few points per CTA) spread a
+            // (point, ECM point) task over LPT lanes: lane c forms component
+            // F_c (double-float), the group exchanges F by shuffles, evaluates
+            // the law redundantly, and lane c writes w P_c, tangent row c and
+            // Y row c -- so the task count NP x CI need not fill the CTA.
+            if constexpr (SPLIT) {
+                constexpr int LPT = G <= 4 ? 4 : 16;
+                const int c = tid % LPT;
+                for (int base = 0; base < NP * CI; base += NT / LPT) {
+                    const int task = base + tid / LPT;
+                    const bool valid = task < NP * CI;
+                    const int p = valid ? task % NP : 0, il = valid ? task / NP : 0;
+                    bool live = valid && (s_flag[p] == ST_OK) && (i0 + il < m);
+                    const int ph = s_ph[buf * CI + il];
+                    df Fc{0.0f, 0.0f};
+                    if (live && c < G) {
+                        const float *Bh = s_Bh + (il * G + c) * BP, *Bl = s_Bl + (il * G + c) * BP;
+                        const float *qh = s_qh + p * QP, *ql = s_ql + p * QP;
+                        dacc sacc{s_Uh[p * G + c], s_Ul[p * G + c]};
+                        for (int j = 0; j < n; ++j) dacc_fma(sacc, Bh[j], Bl[j], qh[j], ql[j]);
+                        Fc = dacc_get(sacc);
+                    }
+                    df F[G];
+#pragma unroll
+                    for (int c2 = 0; c2 < G; ++c2) {
+                        F[c2].hi = __shfl_sync(0xffffffffu, Fc.hi, c2, LPT);
+                        F[c2].lo = __shfl_sync(0xffffffffu, Fc.lo, c2, LPT);
+                    }
+                    df P[G];
+                    float fif[G], lnf = 0.0f;
+                    if (live && !nh_stress_df<D>(F, ph ? dmu1 : dmu0, ph ? dlam1 : dlam0, P, fif, lnf)) {
+                        if (c == 0) atomicCAS(&s_flag[p], ST_OK, ST_DETF);
+                        live = false;  // the same F in every lane of the group: the same decision
+                    }
+                    if (valid && c < G) {
+                        KT *yr = s_Y + ((il * G + c) * NP + p) * NAP;  // row k = il*G + c
+                        if (live) {
+                            df Pc = P[0];
+                            KT fi[G], Ar[G];
+#pragma unroll
+                            for (int c2 = 0; c2 < G; ++c2) {
+                                if (c2 == c) Pc = P[c2];
+                                fi[c2] = (KT)fif[c2];
+                            }
+                            const df wp = df_mul(df{s_wh[il], s_wl[il]}, Pc);
+                            s_WPh[(il * G + c) * NP + p] = wp.hi;
+                            s_WPl[(il * G + c) * NP + p] = wp.lo;
+                            const KT muk = ph ? kmu1 : kmu0, lam = ph ? klam1 : klam0;
+                            const KT c3 = muk - lam * (KT)lnf;
+#pragma unroll
+                            for (int r = 0; r < G; ++r) {  // row c of the tangent (compile-time indices)
+                                KT Ar2[G];
+                                nh_tangent_row<D, KT>(fi, lam, c3, muk, r, Ar2);
+                                if (r == c) {
+#pragma unroll
+                                    for (int c2 = 0; c2 < G; ++c2) Ar[c2] = Ar2[c2];
+                                }
+                            }
+                            const KT *Bx = s_Bx + il * G * NA;
+                            const KT wk = (KT)s_wh[il];
+                            for (int b = 0; b < n; ++b) {
+                                KT v = (KT)0;
+#pragma unroll
+                                for (int c2 = 0; c2 < G; ++c2) v = kfma(Ar[c2], Bx[c2 * NA + b], v);
+                                yr[b] = wk * v;
+                            }
+#pragma unroll
+                            for (int c2 = 0; c2 < G; ++c2) yr[n + c2] = wk * Ar[c2];
+                            for (int b = na; b < NA; ++b) yr[b] = (KT)0;
+                        } else {
+                            s_WPh[(il * G + c) * NP + p] = 0.0f;
+                            s_WPl[(il * G + c) * NP + p] = 0.0f;
+                            for (int b = 0; b < NA; ++b) yr[b] = (KT)0;
+                        }
+                    }
+                }
+            } else
             for (int task = tid; task < NP * CI; task += NT) {
                 const int p = task % NP, il = task / NP;
                 KT *yrow = s_Y + ((il * G) * NP + p) * NAP;  // row k = il*G + c at yrow + c*NP*NAP
