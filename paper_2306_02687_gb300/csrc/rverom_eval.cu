@@ -97,8 +97,13 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, C
         else if (n <= 64) add(RV_FUSED(2, 72, 9, 9, 2, 8, double), "fp64-fused <2,72> 2 points x 8 ECM", 1);
     } else if (dim == 3) {
         if (n <= 47) {
-            if (mixed) add(RV_FUSED(3, 56, 7, 7, 4, 8, float), "simt-fused <3,56> 4 points x 8 ECM", 1);
-            else add(RV_FUSED(3, 56, 7, 7, 2, 4, double), "fp64-fused <3,56> 2 points x 4 ECM", 1);
+            if (mixed) {
+                add(RV_SYM(3, 56, 7, 6, 8, float), "simt-symmetric <3,56> 7x7 blocks, 6 points x 8 ECM", 1);
+                add(RV_SYM(3, 56, 7, 7, 4, float), "simt-symmetric <3,56> 7x7 blocks, 7 points x 4 ECM", 1);
+                add(RV_FUSED(3, 56, 7, 7, 4, 8, float), "simt-fused <3,56> 4 points x 8 ECM", 1);
+            } else {
+                add(RV_FUSED(3, 56, 7, 7, 2, 4, double), "fp64-fused <3,56> 2 points x 4 ECM", 1);
+            }
         }
     }
     for (int i = 0; i < k && i < max_out; ++i) {
