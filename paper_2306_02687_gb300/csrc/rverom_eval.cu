@@ -75,7 +75,9 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, C
             add(RV_SYM(2, 20, 5, 24, 10, float), "simt-symmetric <2,20> 24 points x 10 ECM", 1);
             add(RV_FUSED(2, 20, 5, 5, 16, 16, float), "simt-fused <2,20> 16 points x 16 ECM", 1);
             add(RV_WS(2, 20, 5, 5, 8, 16), "simt-warp-specialized <2,20> 8 points x 16 ECM", 1);
-            add(RV_TC(2, 20, 32, 8), "tcgen05-tf32x3 <2,20> 32 points x 8 ECM + per-thread condensation", 2);
+            // no tensor-core candidate: at 20 columns its accumulation error
+            // leaves too little margin under the 1e-8 stress gate, and the
+            // separate accumulator that fixes it does not fit the 512 TMEM columns
         } else if (n <= 24) {
             add(RV_SYM(2, 28, 7, 24, 10, float), "simt-symmetric <2,28> 24 points x 10 ECM", 1);
             add(RV_FUSED(2, 28, 7, 7, 16, 16, float), "simt-fused <2,28> 16 points x 16 ECM", 1);
@@ -118,7 +120,7 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, C
 int tc_record_words(int dim, int n) {
     if (dim != 2) return 0;
     if (n <= 12) return CondRec<2, 16>::W;
-    if (n <= 16) return CondRec<2, 20>::W;
+    if (n <= 16) return 0;
     if (n <= 24) return CondRec<2, 28>::W;
     return 0;
 }
@@ -227,7 +229,7 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
         td.phase = ph;
         td.Bimg = nullptr;
         td.img_nn = 0;
-        if (ok && dim == 2 && d.n_modes + g <= 32) {
+        if (ok && tc_record_words(dim, d.n_modes) > 0) {  // a tensor-core candidate serves this type
             const int nn = (d.n_modes + g + 15) / 16 * 16;
             std::vector<float> img = tc_table_image(d, g, nn);
             float *bi = nullptr;
