@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     dacc sacc[G];
 #pragma unroll
                     for (int c = 0; c < G; ++c) sacc[c] = dacc{s_Uh[p * G + c], s_Ul[p * G + c]};
+#pragma unroll 4
                     for (int j = 0; j < n; ++j) {
                         const float qhj = qh[j], qlj = ql[j];
 #pragma unroll
@@ -390,25 +391,29 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
 
             // a4: float64-accurate reduced residual and homogenized stress of
             // this warp's points
+            // all of this lane's rows at once (2 RPW independent chains); a row
+            // past the warp's points reads row 0 and is never stored, and rows
+            // j >= n are stored as zero
+            {
+                int bo[RPW], wo[RPW];
 #pragma unroll
-            for (int u = 0; u < RPW; ++u) {
-                const int o = lane + 32 * u;
-                if (o < PPT * NQ) {
-                    const int pl = o / NQ, jj = o % NQ;
-                    if (jj < n) {
-                        dacc v0 = rdacc[2 * u], v1 = rdacc[2 * u + 1];
-                        for (int il = 0; il < CI; il += 2)
-#pragma unroll
-                            for (int c = 0; c < G; ++c) {
-                                const int b0 = (il * G + c) * BP + jj, w0 = (il * G + c) * PPT + pl;
-                                const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
-                                dacc_fma(v0, Bh[b0], Bl[b0], WPh[w0], WPl[w0]);
-                                dacc_fma(v1, Bh[b1], Bl[b1], WPh[w1], WPl[w1]);
-                            }
-                        rdacc[2 * u] = v0;
-                        rdacc[2 * u + 1] = v1;
-                    }
+                for (int u = 0; u < RPW; ++u) {
+                    const int o = lane + 32 * u;
+                    const bool in = o < PPT * NQ;
+                    wo[u] = in ? o / NQ : 0;
+                    bo[u] = in ? o % NQ : 0;
                 }
+#pragma unroll
+                for (int il = 0; il < CI; il += 2)
+#pragma unroll
+                    for (int c = 0; c < G; ++c)
+#pragma unroll
+                        for (int u = 0; u < RPW; ++u) {
+                            const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * PPT + wo[u];
+                            const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
+                            dacc_fma(rdacc[2 * u], Bh[b0], Bl[b0], WPh[w0], WPl[w0]);
+                            dacc_fma(rdacc[2 * u + 1], Bh[b1], Bl[b1], WPh[w1], WPl[w1]);
+                        }
             }
             if (lane < PPT * G) {
                 const int pl = lane / G, c = lane % G;
@@ -508,7 +513,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 const int pl = o / NQ, jj = o % NQ;
                 const int64_t li = tile * NP + p0 + pl;
                 if (li < count) {
-                    const df v = df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1]));
+                    const df v = jj < n ? df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1])) : df{0.0f, 0.0f};
                     float *rec = ws + li * CR::W;
                     rec[CR::o_rh + jj] = v.hi;
                     rec[CR::o_rl + jj] = v.lo;
