@@ -70,12 +70,12 @@ struct TcPlan {
     static constexpr size_t BXPART = (size_t)NN * 32;  // [NN/8][2 kg][8][4] floats
     static constexpr size_t BXBUF = (size_t)KSC * 2 * BXPART;
     static constexpr size_t o_BX = tc_al(o_Y + NW * YWARP);
-    static constexpr size_t NBST = (size_t)CI * G * BP;  // floats per part of a staging buffer
+    static constexpr size_t NBST = (size_t)CI * G * BP;  // (hi, lo) pairs per staging buffer
     static constexpr size_t o_B = tc_al(o_BX + 2 * BXBUF);
     static constexpr size_t o_w = tc_al(o_B + 2 * 2 * NBST * 4);
     static constexpr size_t o_ph = tc_al(o_w + 2 * 2 * CI * 4);
     static constexpr size_t o_W = tc_al(o_ph + 2 * CI * 4);            // [warp][il][p][G*G]
-    static constexpr size_t o_WP = tc_al(o_W + (size_t)NP * CI * G * G * 4);  // hi | lo: [warp][il][c][p]
+    static constexpr size_t o_WP = tc_al(o_W + (size_t)NP * CI * G * G * 4);  // (hi, lo): [warp][il][c][p]
     static constexpr size_t o_q = tc_al(o_WP + 2 * (size_t)NP * CI * G * 4);
     static constexpr size_t o_q64 = tc_al(o_q + 2 * (size_t)NP * QP * 4);
     static constexpr size_t o_U = tc_al(o_q64 + (size_t)NP * QP * 8);
@@ -104,10 +104,10 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     using CR = CondRec<D, NA>;
     extern __shared__ __align__(16) unsigned char smem[];
     float *s_BX = reinterpret_cast<float *>(smem + PL::o_BX);
-    float *s_Bst = reinterpret_cast<float *>(smem + PL::o_B);
+    float2 *s_Bst = reinterpret_cast<float2 *>(smem + PL::o_B);  // (hi, lo) of the B table: [buf][il * G + c][BP]
     float *s_wst = reinterpret_cast<float *>(smem + PL::o_w);
     int *s_ph = reinterpret_cast<int *>(smem + PL::o_ph);
-    float *s_qh = reinterpret_cast<float *>(smem + PL::o_q), *s_ql = s_qh + NP * QP;
+    float2 *s_q2 = reinterpret_cast<float2 *>(smem + PL::o_q);  // (hi, lo) of q: [p][QP]
     double *s_qd = reinterpret_cast<double *>(smem + PL::o_q64);
     double *s_U = reinterpret_cast<double *>(smem + PL::o_U);
     double *s_R = reinterpret_cast<double *>(smem + PL::o_R);
@@ -133,8 +133,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     const int p0 = warp * PPT;
     float *yw = reinterpret_cast<float *>(smem + PL::o_Y + warp * PL::YWARP);
     float *Ww = reinterpret_cast<float *>(smem + PL::o_W) + warp * CI * PPT * G * G;
-    float *WPh = reinterpret_cast<float *>(smem + PL::o_WP) + warp * CI * G * PPT;
-    float *WPl = WPh + NP * CI * G;
+    float2 *WP2 = reinterpret_cast<float2 *>(smem + PL::o_WP) + warp * CI * G * PPT;  // (hi, lo) of w_i P_i
     uint64_t *mbar = s_bar + 2 + 2 * warp;
 
     const df dmu0 = df_from(a.t.mu[0]), dmu1 = df_from(a.t.mu[1]);
@@ -154,7 +153,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         *s_err = 0;
     }
     // staging buffers: zero once (entries past m keep finite values)
-    for (int x = tid; x < 2 * 2 * NBST; x += NT) s_Bst[x] = 0.0f;
+    for (int x = tid; x < 2 * NBST; x += NT) s_Bst[x] = make_float2(0.0f, 0.0f);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -163,14 +162,14 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     uint32_t gstep = 0, gchunk = 0;  // k-steps and chunks issued by this CTA so far
 
     auto stage_cp = [&](int buf, int i0s) {
-        float *bh = s_Bst + buf * 2 * NBST, *bl = bh + NBST;
+        float *b2 = reinterpret_cast<float *>(s_Bst + buf * NBST);
         float *wh = s_wst + buf * 2 * CI, *wl = wh + CI;
         const int cnt = min(CI, m - i0s) * G * n;
         for (int x = tid; x < cnt; x += NT) {
             const int r = x / n, j = x - r * n;  // r = il * G + c
             const int64_t gi = (int64_t)i0s * G * n + x;
-            cp_async4(bh + r * BP + j, a.t.Bh + gi);
-            cp_async4(bl + r * BP + j, a.t.Bl + gi);
+            cp_async4(b2 + 2 * (r * BP + j), a.t.Bh + gi);
+            cp_async4(b2 + 2 * (r * BP + j) + 1, a.t.Bl + gi);
         }
         if (tid < min(CI, m - i0s)) {
             cp_async4(wh + tid, a.t.wh + i0s + tid);
@@ -242,8 +241,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             }
             s_qd[p * QP + j] = qv;
             const df v = df_from(qv);
-            s_qh[p * QP + j] = v.hi;
-            s_ql[p * QP + j] = v.lo;
+            s_q2[p * QP + j] = make_float2(v.hi, v.lo);
         }
         dacc rdacc[2 * RPW];
 #pragma unroll
@@ -267,7 +265,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 stage_cp(buf ^ 1, i0 + CI);
                 if (tid == 0) stage_bulk(buf ^ 1, ch + 1);
             }
-            const float *Bh = s_Bst + buf * 2 * NBST, *Bl = Bh + NBST;
+            const float2 *B2 = s_Bst + buf * NBST;
             const float *wh = s_wst + buf * 2 * CI, *wl = wh + CI;
 
             // pointwise (this warp's points, one ECM point per lane):
@@ -281,16 +279,19 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 float lnJk = 0.0f;
                 if (live) {
                     df F[G], P[G];
-                    const float *bh = Bh + il * G * BP, *bl = Bl + il * G * BP;
-                    const float *qh = s_qh + p * QP, *ql = s_ql + p * QP;
+                    const float2 *b2 = B2 + il * G * BP;
+                    const float2 *q2 = s_q2 + p * QP;
                     dacc sacc[G];
 #pragma unroll
                     for (int c = 0; c < G; ++c) sacc[c] = dacc{s_Uh[p * G + c], s_Ul[p * G + c]};
 #pragma unroll 4
                     for (int j = 0; j < n; ++j) {
-                        const float qhj = qh[j], qlj = ql[j];
+                        const float2 qj = q2[j];
 #pragma unroll
-                        for (int c = 0; c < G; ++c) dacc_fma(sacc[c], bh[c * BP + j], bl[c * BP + j], qhj, qlj);
+                        for (int c = 0; c < G; ++c) {
+                            const float2 bj = b2[c * BP + j];
+                            dacc_fma(sacc[c], bj.x, bj.y, qj.x, qj.y);
+                        }
                     }
 #pragma unroll
                     for (int c = 0; c < G; ++c) F[c] = dacc_get(sacc[c]);
@@ -302,8 +303,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
 #pragma unroll
                         for (int c = 0; c < G; ++c) {
                             const df wp = df_mul(w2, P[c]);
-                            WPh[(il * G + c) * PPT + pl] = wp.hi;
-                            WPl[(il * G + c) * PPT + pl] = wp.lo;
+                            WP2[(il * G + c) * PPT + pl] = make_float2(wp.hi, wp.lo);
                         }
                     }
                 }
@@ -321,8 +321,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 } else {
 #pragma unroll
                     for (int c = 0; c < G; ++c) {
-                        WPh[(il * G + c) * PPT + pl] = 0.0f;
-                        WPl[(il * G + c) * PPT + pl] = 0.0f;
+                        WP2[(il * G + c) * PPT + pl] = make_float2(0.0f, 0.0f);
                         Wt[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     }
                 }
@@ -342,7 +341,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     const int il = ks * EPS + e;
                     float bx[G];
 #pragma unroll
-                    for (int d = 0; d < G; ++d) bx[d] = (j < n) ? Bh[(il * G + d) * BP + j] : ((j - n == d) ? 1.0f : 0.0f);
+                    for (int d = 0; d < G; ++d) bx[d] = (j < n) ? B2[(il * G + d) * BP + j].x : ((j - n == d) ? 1.0f : 0.0f);
                     const bool jin = j < na;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -411,14 +410,17 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                         for (int u = 0; u < RPW; ++u) {
                             const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * PPT + wo[u];
                             const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
-                            dacc_fma(rdacc[2 * u], Bh[b0], Bl[b0], WPh[w0], WPl[w0]);
-                            dacc_fma(rdacc[2 * u + 1], Bh[b1], Bl[b1], WPh[w1], WPl[w1]);
+                            const float2 x0 = B2[b0], y0 = WP2[w0], x1 = B2[b1], y1 = WP2[w1];
+                            dacc_fma(rdacc[2 * u], x0.x, x0.y, y0.x, y0.y);
+                            dacc_fma(rdacc[2 * u + 1], x1.x, x1.y, y1.x, y1.y);
                         }
             }
             if (lane < PPT * G) {
                 const int pl = lane / G, c = lane % G;
-                for (int il = 0; il < CI; ++il)
-                    pudf = df_add(pudf, df{WPh[(il * G + c) * PPT + pl], WPl[(il * G + c) * PPT + pl]});
+                for (int il = 0; il < CI; ++il) {
+                    const float2 v = WP2[(il * G + c) * PPT + pl];
+                    pudf = df_add(pudf, df{v.x, v.y});
+                }
             }
 
             // fold the chunk accumulators into the running sums (TMEM), Kahan-
