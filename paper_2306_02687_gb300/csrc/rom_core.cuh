@@ -1297,9 +1297,15 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
                     if (live && c < G) {
                         const float *Bh = s_Bh + (il * G + c) * BP, *Bl = s_Bl + (il * G + c) * BP;
                         const float *qh = s_qh + p * QP, *ql = s_ql + p * QP;
-                        dacc sacc{s_Uh[p * G + c], s_Ul[p * G + c]};
-                        for (int j = 0; j < n; ++j) dacc_fma(sacc, Bh[j], Bl[j], qh[j], ql[j]);
-                        Fc = dacc_get(sacc);
+                        // four partial sums over j mod 4 (independent chains)
+                        dacc s4[4] = {{s_Uh[p * G + c], s_Ul[p * G + c]}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+                        int j = 0;
+                        for (; j + 4 <= n; j += 4) {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) dacc_fma(s4[t], Bh[j + t], Bl[j + t], qh[j + t], ql[j + t]);
+                        }
+                        for (; j < n; ++j) dacc_fma(s4[0], Bh[j], Bl[j], qh[j], ql[j]);
+                        Fc = df_add(df_add(dacc_get(s4[0]), dacc_get(s4[1])), df_add(dacc_get(s4[2]), dacc_get(s4[3])));
                     }
                     df F[G];
 #pragma unroll
@@ -1371,6 +1377,7 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
                         dacc sacc[G];
 #pragma unroll
                         for (int c = 0; c < G; ++c) sacc[c] = dacc{s_Uh[p * G + c], s_Ul[p * G + c]};
+#pragma unroll 4
                         for (int j = 0; j < n; ++j) {
                             const float qhj = qh[j], qlj = ql[j];
 #pragma unroll
@@ -1486,26 +1493,27 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
             }
             // float64-accurate reduced residual and homogenized stress
             if (MIX) {
+                // all of this thread's rows at once (2 RPT independent chains);
+                // a row past the CTA's points reads row 0 and is never stored,
+                // rows j >= n are stored as zero
+                int bo[RPT], wo[RPT];
 #pragma unroll
                 for (int u = 0; u < RPT; ++u) {
                     const int o = tid + u * NT;
-                    if (o < NP * NQ) {
-                        const int p = o / NQ, j = o % NQ;
-                        if (j < n) {
-                            dacc v0 = rdacc[2 * u], v1 = rdacc[2 * u + 1];
-                            for (int il = 0; il < CI; il += 2)
-#pragma unroll
-                                for (int c = 0; c < G; ++c) {
-                                    const int b0 = (il * G + c) * BP + j, w0 = (il * G + c) * NP + p;
-                                    const int b1 = b0 + G * BP, w1 = w0 + G * NP;
-                                    dacc_fma(v0, s_Bh[b0], s_Bl[b0], s_WPh[w0], s_WPl[w0]);
-                                    dacc_fma(v1, s_Bh[b1], s_Bl[b1], s_WPh[w1], s_WPl[w1]);
-                                }
-                            rdacc[2 * u] = v0;
-                            rdacc[2 * u + 1] = v1;
-                        }
-                    }
+                    const bool in = o < NP * NQ;
+                    wo[u] = in ? o / NQ : 0;
+                    bo[u] = in ? o % NQ : 0;
                 }
+                for (int il = 0; il < CI; il += 2)
+#pragma unroll
+                    for (int c = 0; c < G; ++c)
+#pragma unroll
+                        for (int u = 0; u < RPT; ++u) {
+                            const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * NP + wo[u];
+                            const int b1 = b0 + G * BP, w1 = w0 + G * NP;
+                            dacc_fma(rdacc[2 * u], s_Bh[b0], s_Bl[b0], s_WPh[w0], s_WPl[w0]);
+                            dacc_fma(rdacc[2 * u + 1], s_Bh[b1], s_Bl[b1], s_WPh[w1], s_WPl[w1]);
+                        }
             } else {
 #pragma unroll
                 for (int u = 0; u < RPT; ++u) {
@@ -1550,7 +1558,7 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
             for (int u = 0; u < RPT; ++u) {
                 const int o = tid + u * NT;
                 if (o < NP * NQ) {
-                    const df v = df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1]));
+                    const df v = (o % NQ) < n ? df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1])) : df{0.0f, 0.0f};
                     s_rh[o] = v.hi;
                     s_rl[o] = v.lo;
                 }
