@@ -84,9 +84,11 @@ struct TcPlan {
     static constexpr size_t o_Udf = tc_al(o_dU + (size_t)NP * NS * 8);
     static constexpr size_t o_flag = tc_al(o_Udf + 2 * (size_t)NP * G * 4);
     static constexpr size_t o_pidx = o_flag + NP * 4;
-    // mbarriers: [0,1] table copies, [2 + 2 w + b] MMA commits of warp w; then TMEM slot, error flag
+    // mbarriers: [0,1] table copies, [2 + 2 w + b] MMA commits of warp w per
+    // A buffer, [2 + 2 NW + w] MMAs of a whole chunk of warp w; then TMEM
+    // slot, error flag
     static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);
-    static constexpr size_t o_slot = o_bar + (2 + 2 * NW) * 8;
+    static constexpr size_t o_slot = o_bar + (2 + 3 * NW) * 8;
     static constexpr size_t bytes = tc_al(o_slot + 8);
     static_assert(bytes <= 227 * 1024, "shared memory");
 };
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     int *s_pidx = reinterpret_cast<int *>(smem + PL::o_pidx);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + PL::o_bar);
     uint32_t *s_slot = reinterpret_cast<uint32_t *>(smem + PL::o_slot);
-    int *s_err = reinterpret_cast<int *>(smem + PL::o_slot + 4);
+    volatile int *s_err = reinterpret_cast<volatile int *>(smem + PL::o_slot + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n = a.t.n, m = a.t.m;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int b = 0; b < 2 + 2 * NW; ++b) tc::mbar_init(&s_bar[b], 1);
+        for (int b = 0; b < 2 + 3 * NW; ++b) tc::mbar_init(&s_bar[b], 1);
         tc::mbar_init_fence();
         *s_err = 0;
     }
@@ -159,6 +161,11 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     tc::fence_after_sync();
     const uint32_t tbase = *s_slot;
     const uint32_t idesc = tc::idesc_tf32(128, NN);
+    // bounded wait; after the first timeout no wait blocks any more (the
+    // tile's points are then marked ST_TIMEOUT)
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (*s_err == 0 && !tc::mbar_wait(bar, parity)) *s_err = 1;
+    };
     uint32_t gstep = 0, gchunk = 0;  // k-steps and chunks issued by this CTA so far
 
     auto stage_cp = [&](int buf, int i0s) {
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             for (int ks = 0; ks < KSC; ++ks) {
                 const uint32_t s = gstep + ks;
                 const int yb = s & 1;
-                if (s >= 2 && !tc::mbar_wait(&mbar[yb], ((s - 2) >> 1) & 1)) *s_err = 1;
+                if (s >= 2) wait(&mbar[yb], ((s - 2) >> 1) & 1);
                 float *Yh = yw + yb * 2048, *Yl = Yh + 1024;
 #pragma unroll
                 for (int e = 0; e < EPS; ++e) {
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) {
-                    if (ks == 0 && !tc::mbar_wait(&s_bar[buf], (gchunk >> 1) & 1)) *s_err = 1;
+                    if (ks == 0) wait(&s_bar[buf], (gchunk >> 1) & 1);
                     tc::fence_after_sync();
                     const uint32_t ba = tc::smem_u32(s_BX + buf * (PL::BXBUF / 4) + ks * 2 * (PL::BXPART / 4));
                     const uint64_t bdh = tc::smem_desc(ba, 128, 256);
@@ -383,6 +390,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     tc::mma_tf32(dt, adh, bdl, idesc, 1u);
                     tc::mma_tf32(dt, adl, bdh, idesc, 1u);
                     tc::mma_commit(&mbar[yb]);
+                    if (ks == KSC - 1) tc::mma_commit(&s_bar[2 + 2 * NW + warp]);  // the whole chunk
                 }
                 __syncwarp();
             }
@@ -428,13 +436,15 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             // accumulator, onto which the next chunk's MMAs add, so the next
             // fold adds (chunk sum - compensation).  The last fold writes the
             // augmented system of every point to the workspace.  A warp reads
-            // its lane quarter of every other tile, so it waits for the last
-            // commit of every warp.
+            // its lane quarter of every other tile, so it waits for the chunk
+            // barrier of every warp: one phase per chunk, so the phase waited
+            // for is always the barrier's current one or the one before it (a
+            // parity wait is defined only for those two; the per-buffer
+            // barriers advance twice per chunk and would not do).
             const bool last = (ch == nch - 1);
             {
-                const uint32_t sl = gstep - 1;
                 for (int w2 = 0; w2 < NW; ++w2)
-                    if (!tc::mbar_wait(&s_bar[2 + 2 * w2 + (sl & 1)], (sl >> 1) & 1)) *s_err = 1;
+                    wait(&s_bar[2 + 2 * NW + w2], gchunk & 1);
                 __syncwarp();  // the TMEM loads below are warp-collective
                 tc::fence_after_sync();
                 const int qd = warp & 3;

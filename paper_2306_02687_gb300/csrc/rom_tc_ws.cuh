@@ -1,0 +1,572 @@
+// rom_tc_ws.cuh -- warp-specialized variant of the tensor-core evaluation
+// kernel (steps a1-a5 of Sec. 3.2, Eqs. ROMintforce, ROMstiffness; the
+// contraction of Eq. Biot_Tangent's augmented system on tcgen05).
+//
+// Same arithmetic and workspace records as eval_tc_kernel (rom_tc.cuh); the
+// work of a chunk of CI ECM points is split between two roles:
+//  - 8 tile warps (warpgroups 0, 1): each owns one 128-row MMA tile (PPT
+//    points) -- kinematics and law for its points (double-float), w_i P_i,
+//    w_i A_i, the A-operand build and the MMA issue;
+//  - 4 helper warps (warpgroup 2), helper warp h serving TMEM lane quarter h:
+//    the Kahan-compensated fold of the accumulators of all 8 tiles, the
+//    float64-accurate residual and homogenized stress of all points, the
+//    staging of the tables of later chunks and the workspace records.
+// The tile warps go from one chunk's MMAs straight to the next chunk's law,
+// so the fold and the residual of chunk c overlap the law and the A build of
+// chunk c + 1; the only CTA barriers are at the start and the end of a tile of
+// NP points.  Hand-offs, all mbarriers with bounded waits:
+//   staged[b]  tables of a chunk in buffer b landed (cp.async arrivals)
+//   bx[b]      B-operand image of a chunk in buffer b landed (bulk copy)
+//   commit[w]  MMAs of tile warp w (per A buffer) completed
+//   chunk[w]   MMAs of a whole chunk of tile warp w completed
+//   wp[b]      w_i P_i of a chunk written by every tile warp (buffer b)
+//   res[b]     residual of the chunk in buffer b done (w P buffer free)
+//   fold       accumulators of the last chunk folded (accumulators free)
+// Registers: the block is launched with 168 per thread (384 threads); tile
+// warps raise theirs to 184 and helper warps lower theirs to 136
+// (8 x 32 x 184 + 4 x 32 x 136 = 384 x 168; the fold and the residual of all
+// points need more registers than the law of one point per lane); the launcher
+// checks the compiled count.
+#pragma once
+
+#include "rom_tc.cuh"
+
+namespace rverom {
+
+template <int D, int NA, int NP, int CI>
+struct TcWsPlan {
+    static constexpr int G = D * D;
+    static constexpr int NS = Dims<D>::NS;
+    static constexpr int NQ = NA - G;
+    static constexpr int QP = NQ | 1;
+    static constexpr int BP = NQ | 1;
+    static constexpr int NAR = NA <= 16 ? 16 : 32;  // A-operand rows per point
+    static constexpr int PPT = 128 / NAR;           // points per 128-row tile
+    static constexpr int NN = (NA + 15) / 16 * 16;  // MMA N (columns of Bext)
+    static constexpr int NW = 8;                    // tile warps = tiles
+    static constexpr int NH = 4;                    // helper warps (one per TMEM lane quarter)
+    static constexpr int NT = 32 * (NW + NH);
+    static constexpr int NHT = 32 * NH;             // helper threads
+    static constexpr int REGS_LAUNCH = 168, REGS_TILE = 184, REGS_HELP = 136;
+    static constexpr int EPS = 8 / G;               // ECM points per k-step of 8
+    static constexpr int KSC = CI / EPS;            // k-steps per chunk
+    static constexpr int RPH = (NP * NQ + NHT - 1) / NHT;  // residual rows per helper thread
+    static constexpr int TCOLS = 2 * NW * NN;       // accumulator + running sum
+    static constexpr int TALLOC = TCOLS <= 32 ? 32 : TCOLS <= 64 ? 64 : TCOLS <= 128 ? 128 : TCOLS <= 256 ? 256 : 512;
+    static_assert(D == 2, "planar RVEs (two ECM points per k-step)");
+    static_assert(NA <= 32, "record layout of the per-thread condensation");
+    static_assert(NP == NW * PPT, "one tile per tile warp");
+    static_assert(CI * PPT == 32, "one law evaluation per lane and chunk");
+    static_assert(CI % EPS == 0 && CI % 2 == 0, "a chunk holds whole k-steps");
+    static_assert(NN % 16 == 0, "fold in blocks of 16 columns");
+    static_assert(NP * G <= NHT, "one homogenized-stress entry per helper thread");
+    static_assert(TCOLS <= 512, "TMEM holds 512 columns");
+    static_assert(NW * 32 * REGS_TILE + NH * 32 * REGS_HELP == NT * REGS_LAUNCH, "register split");
+    // byte offsets
+    static constexpr size_t YWARP = 4 * 4096;  // per tile warp: [2 buffers][hi|lo][2 kg][16 rg][8][4] floats
+    static constexpr size_t o_Y = 0;
+    static constexpr size_t BXPART = (size_t)NN * 32;
+    static constexpr size_t BXBUF = (size_t)KSC * 2 * BXPART;
+    static constexpr size_t o_BX = tc_al(o_Y + NW * YWARP);
+    static constexpr size_t NBST = (size_t)CI * G * BP;  // (hi, lo) pairs per staging buffer
+    static constexpr size_t o_B = tc_al(o_BX + 2 * BXBUF);
+    static constexpr size_t o_w = tc_al(o_B + 2 * NBST * 8);
+    static constexpr size_t o_ph = tc_al(o_w + 2 * 2 * CI * 4);
+    static constexpr size_t o_W = tc_al(o_ph + 2 * CI * 4);                  // [warp][il][p][G*G]
+    static constexpr size_t WPBUF = (size_t)NP * CI * G;                     // (hi, lo) pairs per buffer
+    static constexpr size_t o_WP = tc_al(o_W + (size_t)NP * CI * G * G * 4);  // [2][warp][il][c][p]
+    static constexpr size_t o_q = tc_al(o_WP + 2 * WPBUF * 8);
+    static constexpr size_t o_q64 = tc_al(o_q + (size_t)NP * QP * 8);
+    static constexpr size_t o_U = tc_al(o_q64 + (size_t)NP * QP * 8);
+    static constexpr size_t o_R = tc_al(o_U + (size_t)NP * G * 8);
+    static constexpr size_t o_dU = tc_al(o_R + (size_t)NP * G * 8);
+    static constexpr size_t o_Udf = tc_al(o_dU + (size_t)NP * NS * 8);
+    static constexpr size_t o_flag = tc_al(o_Udf + 2 * (size_t)NP * G * 4);
+    static constexpr size_t o_pidx = o_flag + NP * 4;
+    // mbarriers: bx[2], commit[NW][2], staged[2], wp[2], res[2], fold, chunk[NW]
+    static constexpr int NBAR = 2 + 2 * NW + 2 + 2 + 2 + 1 + NW;
+    static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);
+    static constexpr size_t o_slot = o_bar + NBAR * 8;
+    static constexpr size_t bytes = tc_al(o_slot + 8);
+    static_assert(bytes <= 227 * 1024, "shared memory");
+};
+
+template <int D, int NA, int NP, int CI>
+__global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
+    using PL = TcWsPlan<D, NA, NP, CI>;
+    constexpr int G = PL::G, NS = PL::NS, NQ = PL::NQ, QP = PL::QP, BP = PL::BP;
+    constexpr int NAR = PL::NAR, PPT = PL::PPT, NN = PL::NN, NW = PL::NW, NH = PL::NH;
+    constexpr int EPS = PL::EPS, KSC = PL::KSC, NT = PL::NT, NHT = PL::NHT, RPH = PL::RPH;
+    constexpr int NBST = (int)PL::NBST, WPBUF = (int)PL::WPBUF;
+    using CR = CondRec<D, NA>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *s_BX = reinterpret_cast<float *>(smem + PL::o_BX);
+    float2 *s_Bst = reinterpret_cast<float2 *>(smem + PL::o_B);  // (hi, lo) of the B table: [buf][il * G + c][BP]
+    float *s_wst = reinterpret_cast<float *>(smem + PL::o_w);
+    int *s_ph = reinterpret_cast<int *>(smem + PL::o_ph);
+    float *s_W = reinterpret_cast<float *>(smem + PL::o_W);
+    float2 *s_WP = reinterpret_cast<float2 *>(smem + PL::o_WP);  // (hi, lo) of w_i P_i
+    float2 *s_q2 = reinterpret_cast<float2 *>(smem + PL::o_q);    // (hi, lo) of q: [p][QP]
+    double *s_qd = reinterpret_cast<double *>(smem + PL::o_q64);
+    double *s_U = reinterpret_cast<double *>(smem + PL::o_U);
+    double *s_R = reinterpret_cast<double *>(smem + PL::o_R);
+    double *s_dU = reinterpret_cast<double *>(smem + PL::o_dU);
+    float *s_Uh = reinterpret_cast<float *>(smem + PL::o_Udf), *s_Ul = s_Uh + NP * G;
+    int *s_flag = reinterpret_cast<int *>(smem + PL::o_flag);
+    int *s_pidx = reinterpret_cast<int *>(smem + PL::o_pidx);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + PL::o_bar);
+    uint64_t *b_bx = s_bar, *b_commit = s_bar + 2, *b_staged = b_commit + 2 * NW;
+    uint64_t *b_wp = b_staged + 2, *b_res = b_wp + 2, *b_fold = b_res + 2, *b_chunk = b_fold + 1;
+    uint32_t *s_slot = reinterpret_cast<uint32_t *>(smem + PL::o_slot);
+    volatile int *s_err = reinterpret_cast<volatile int *>(smem + PL::o_slot + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool helper = warp >= NW;
+    const int n = a.t.n, m = a.t.m;
+    const int na = n + G;
+    const int64_t count = a.count ? (int64_t)(*a.count) : a.n_points;
+    const int64_t off = (a.perm && a.offset) ? (int64_t)(*a.offset) : 0;
+    const int32_t *perm = a.perm ? a.perm + off : nullptr;
+    float *ws = a.cond + off * CR::W;  // records of this type's points, by list position
+    const int64_t n_tiles = (count + NP - 1) / NP;
+    const int nch = (m + CI - 1) / CI;
+
+    if (warp == 0) {
+        tc::tmem_alloc(s_slot, PL::TALLOC);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2 + 2 * NW; ++b) tc::mbar_init(&s_bar[b], 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&b_staged[b], NHT);
+            tc::mbar_init(&b_wp[b], NW);
+            tc::mbar_init(&b_res[b], NH);
+        }
+        tc::mbar_init(b_fold, NH);
+        for (int w = 0; w < NW; ++w) tc::mbar_init(&b_chunk[w], 1);
+        tc::mbar_init_fence();
+        *s_err = 0;
+    }
+    // staging buffers: zero once (entries past m keep finite values)
+    for (int x = tid; x < 2 * NBST; x += NT) s_Bst[x] = make_float2(0.0f, 0.0f);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // Each role runs its own copy of the tile loop right after its register
+    // reallocation (so that the compiler sees one register budget per role);
+    // the CTA-wide barriers (id 0) of the two copies pair up: A after the
+    // polar split and micro update, B after the chunks, C after the records.
+    // bounded wait; after the first timeout no wait blocks any more (the
+    // tile's points are then marked ST_TIMEOUT)
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (*s_err == 0 && !tc::mbar_wait(bar, parity)) *s_err = 1;
+    };
+    // helper threads: tables of chunk ch (CTA-wide chunk index g) into buffer g & 1
+    auto stage = [&](uint32_t g, int ch) {
+        const int b = g & 1, i0s = ch * CI, ht = tid - NW * 32;
+        float *b2 = reinterpret_cast<float *>(s_Bst + b * NBST);
+        float *wh = s_wst + b * 2 * CI, *wl = wh + CI;
+        const int cnt = min(CI, m - i0s) * G * n;
+        for (int x = ht; x < cnt; x += NHT) {
+            const int r = x / n, j = x - r * n;  // r = il * G + c
+            const int64_t gi = (int64_t)i0s * G * n + x;
+            cp_async4(b2 + 2 * (r * BP + j), a.t.Bh + gi);
+            cp_async4(b2 + 2 * (r * BP + j) + 1, a.t.Bl + gi);
+        }
+        if (ht < min(CI, m - i0s)) {
+            cp_async4(wh + ht, a.t.wh + i0s + ht);
+            cp_async4(wl + ht, a.t.wl + i0s + ht);
+            cp_async4(s_ph + b * CI + ht, a.t.phase + i0s + ht);
+        }
+        tc::cp_async_mbar_arrive(&b_staged[b]);
+        if (ht == 0) {
+            tc::mbar_arrive_expect_tx(&b_bx[b], (uint32_t)PL::BXBUF);
+            tc::bulk_g2s(s_BX + b * (PL::BXBUF / 4), a.t.Bimg + (size_t)ch * (PL::BXBUF / 4), (uint32_t)PL::BXBUF,
+                         &b_bx[b]);
+        }
+    };
+
+    const uint32_t tbase_init = *s_slot;
+    if (helper) {
+        // ===================== helper warps =====================================
+        tc::regs_dec<PL::REGS_HELP>();
+        const uint32_t tbase = tbase_init;
+        uint32_t gc = 0, gstep = 0;  // chunks and k-steps of this CTA before the current tile
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            // tables of the first two chunks (the buffers are free since barrier C)
+            stage(gc, 0);
+            if (nch > 1) stage(gc + 1, 1);
+            tc::named_bar(0, NT);  // A
+            dacc rdacc[2 * RPH];
+            df pudf{0.0f, 0.0f};
+            const int ht = tid - NW * 32, qd = warp & 3;
+            const uint32_t lanes = (uint32_t)(qd * 32) << 16;
+            // residual rows o = ht + NHT u: point o / NQ, mode o % NQ
+            int bo[RPH], wo[RPH];
+#pragma unroll
+            for (int u = 0; u < RPH; ++u) {
+                const int o = ht + NHT * u;
+                const bool in = o < NP * NQ;
+                const int p = in ? o / NQ : 0;
+                bo[u] = in ? o % NQ : 0;
+                wo[u] = (p / PPT) * CI * G * PPT + p % PPT;  // w P of point p: [warp][il][c][pl]
+            }
+#pragma unroll
+            for (int u = 0; u < 2 * RPH; ++u) rdacc[u] = dacc{0.0f, 0.0f};
+            const int pp = ht / G, pc = ht % G;  // homogenized-stress entry of this thread
+            const int pwo = (pp / PPT) * CI * G * PPT + pp % PPT;
+
+            for (int ch = 0; ch < nch; ++ch) {
+                const uint32_t g = gc + ch;
+                const int b = g & 1;
+                const bool last = (ch == nch - 1);
+                // fold: wait for the last commit of the chunk of every tile
+                // warp, then fold lane quarter qd of every tile, Kahan-
+                // compensated (the negated compensation goes into the
+                // accumulator, onto which the next chunk's MMAs add); the last
+                // fold writes the augmented systems to the workspace
+                {
+                    // chunk barriers: one phase per chunk; tile warp w cannot
+                    // commit chunk g + 1 before this fold released the
+                    // accumulators, so phase g is the barrier's current phase
+                    // or the one before it (a parity wait is defined only for
+                    // those two)
+                    for (int w2 = 0; w2 < NW; ++w2) wait(&b_chunk[w2], g & 1);
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    const bool kahan = ch > 0;
+                    for (int t = 0; t < NW; ++t) {
+                        const int row = t * 128 + qd * 32 + lane;
+                        const int p = row / NAR, jr = row % NAR;
+#pragma unroll
+                        for (int cb = 0; cb < NN / 16; ++cb) {
+                            const uint32_t ca = tbase + lanes + t * NN + cb * 16;
+                            float va[16], vs[16];
+                            tc::tmem_ld16(ca, va);
+                            if (kahan) tc::tmem_ld16(ca + NW * NN, vs);
+                            tc::tmem_wait_ld();
+                            if (kahan) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) {
+                                    const float tt = __fadd_rn(vs[c], va[c]);
+                                    vs[c] = __fsub_rn(va[c], __fsub_rn(tt, vs[c]));  // -(compensation)
+                                    va[c] = tt;
+                                }
+                                if (!last) tc::tmem_st16(ca, vs);
+                            }
+                            if (!last) {
+                                tc::tmem_st16(ca + NW * NN, va);
+                            } else if (jr < NA && tile * NP + p < count) {
+                                // lane jr holds column jr of M: entries (col, jr), col >= jr
+                                float *rm = ws + (tile * NP + p) * CR::W + CR::o_M;
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) {
+                                    const int col = cb * 16 + c;
+                                    if (col < NA && col >= jr) rm[tri(col, jr)] = va[c];
+                                }
+                            }
+                        }
+                    }
+                    if (!last) tc::tmem_wait_st();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(b_fold);
+                }
+                // a4: residual and homogenized stress of chunk ch (double-float)
+                wait(&b_wp[b], (g >> 1) & 1);
+                wait(&b_staged[b], (g >> 1) & 1);
+                {
+                    const float2 *B2 = s_Bst + b * NBST;
+                    const float2 *WP = s_WP + b * WPBUF;
+#pragma unroll 1
+                    for (int il = 0; il < CI; il += 2)
+#pragma unroll
+                        for (int c = 0; c < G; ++c)
+#pragma unroll
+                            for (int u = 0; u < RPH; ++u) {
+                                const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * PPT + wo[u];
+                                const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
+                                const float2 x0 = B2[b0], y0 = WP[w0], x1 = B2[b1], y1 = WP[w1];
+                                dacc_fma(rdacc[2 * u], x0.x, x0.y, y0.x, y0.y);
+                                dacc_fma(rdacc[2 * u + 1], x1.x, x1.y, y1.x, y1.y);
+                            }
+                    if (ht < NP * G) {
+                        for (int il = 0; il < CI; ++il) {
+                            const float2 v = WP[(il * G + pc) * PPT + pwo];
+                            pudf = df_add(pudf, df{v.x, v.y});
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&b_res[b]);
+                // refill buffer b with chunk ch + 2 once every helper warp is
+                // done with chunk ch (the tile warps are: their commits came in)
+                if (ch + 2 < nch) {
+                    tc::named_bar(1, NHT);
+                    stage(g + 2, ch + 2);
+                }
+            }
+            tc::named_bar(0, NT);  // B: every warp done with the tile's chunks (flags final)
+            // ---- workspace records (steps a6, a7 follow in condense_kernel):
+            // residual and V0 Pbar_U (double-float), q, R, U, status
+            const int err = *s_err;
+#pragma unroll
+            for (int u = 0; u < RPH; ++u) {
+                const int o = ht + NHT * u;
+                if (o < NP * NQ) {
+                    const int p = o / NQ, jj = o % NQ;
+                    const int64_t li = tile * NP + p;
+                    if (li < count) {
+                        const df v = jj < n ? df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1])) : df{0.0f, 0.0f};
+                        float *rec = ws + li * CR::W;
+                        rec[CR::o_rh + jj] = v.hi;
+                        rec[CR::o_rl + jj] = v.lo;
+                        reinterpret_cast<double *>(rec + CR::o_q)[jj] = s_qd[p * QP + jj];
+                    }
+                }
+            }
+            if (ht < NP * G) {
+                const int64_t li = tile * NP + pp;
+                if (li < count) {
+                    float *rec = ws + li * CR::W;
+                    rec[CR::o_ph + pc] = pudf.hi;
+                    rec[CR::o_pl + pc] = pudf.lo;
+                    reinterpret_cast<double *>(rec + CR::o_R)[pc] = s_R[pp * G + pc];
+                    reinterpret_cast<double *>(rec + CR::o_U)[pc] = s_U[pp * G + pc];
+                    if (pc == 0) *reinterpret_cast<int *>(rec + CR::o_flag) = err ? ST_TIMEOUT : s_flag[pp];
+                }
+            }
+            gc += (uint32_t)nch;
+            gstep += (uint32_t)(nch * KSC);
+            tc::named_bar(0, NT);  // C: records written before the next tile's a1
+        }
+    } else {
+        // ===================== tile warps =======================================
+        tc::regs_inc<PL::REGS_TILE>();
+        constexpr int NTT = 32 * NW;
+        const uint32_t tbase = tbase_init;
+        uint32_t gc = 0, gstep = 0;
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            // ---- a1: polar split, micro update ------------------------------
+            if (tid < NP) {
+                const int p = tid;
+                const int64_t li = tile * NP + p;
+                int gp = -1;
+                if (li < count) gp = perm ? perm[li] : (int)li;
+                s_pidx[p] = gp;
+                int flag = -1;
+                double F[G], R[G], U[G];
+                if (gp >= 0) {
+                    flag = ST_OK;
+                    bool fin = true;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        F[c] = a.Fbar[(int64_t)gp * G + c];
+                        fin = fin && isfinite(F[c]);
+                    }
+                    if (!fin) flag = ST_NONFINITE;
+                    else if (!(det<D>(F) > 0.0) || !polar<D>(F, R, U)) flag = ST_DETF;
+                }
+                if (flag != ST_OK) {
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        R[c] = (c % (D + 1) == 0) ? 1.0 : 0.0;
+                        U[c] = R[c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < G; ++c) {
+                    s_U[p * G + c] = U[c];
+                    s_R[p * G + c] = R[c];
+                    const df u = df_from(U[c]);
+                    s_Uh[p * G + c] = u.hi;
+                    s_Ul[p * G + c] = u.lo;
+                }
+#pragma unroll
+                for (int v = 0; v < NS; ++v) {
+                    int i, j;
+                    voigt_pair(D, v, i, j);
+                    s_dU[p * NS + v] = (flag == ST_OK) ? U[i * D + j] - a.Uprev[(int64_t)gp * NS + v] : 0.0;
+                }
+                s_flag[p] = flag;
+            }
+            tc::named_bar(2, NTT);
+            for (int x = tid; x < NP * NQ; x += NTT) {
+                const int p = x / NQ, j = x % NQ;
+                const int gp = s_pidx[p];
+                double qv = 0.0;
+                if (j < n && gp >= 0 && s_flag[p] == ST_OK) {
+                    const int64_t base = (int64_t)gp * a.nmax + j;
+                    qv = a.q[base] - a.s[base];
+#pragma unroll
+                    for (int v = 0; v < NS; ++v) qv -= a.S[base * NS + v] * s_dU[p * NS + v];
+                }
+                s_qd[p * QP + j] = qv;
+                const df v = df_from(qv);
+                s_q2[p * QP + j] = make_float2(v.hi, v.lo);
+            }
+            tc::named_bar(0, NT);  // A
+            const int p0 = warp * PPT;
+            float *yw = reinterpret_cast<float *>(smem + PL::o_Y + warp * PL::YWARP);
+            float *Ww = s_W + warp * CI * PPT * G * G;
+            uint64_t *mbar = b_commit + 2 * warp;
+            const uint32_t idesc = tc::idesc_tf32(128, NN);
+            const df dmu0 = df_from(a.t.mu[0]), dmu1 = df_from(a.t.mu[1]);
+            const df dlam0 = df_from(a.t.kappa[0] - (2.0 / 3.0) * a.t.mu[0]);
+            const df dlam1 = df_from(a.t.kappa[1] - (2.0 / 3.0) * a.t.mu[1]);
+            const float kmu0 = (float)a.t.mu[0], kmu1 = (float)a.t.mu[1];
+            const float klam0 = (float)(a.t.kappa[0] - (2.0 / 3.0) * a.t.mu[0]);
+            const float klam1 = (float)(a.t.kappa[1] - (2.0 / 3.0) * a.t.mu[1]);
+
+            for (int ch = 0; ch < nch; ++ch) {
+                const uint32_t g = gc + ch;
+                const int b = g & 1;
+                const int i0 = ch * CI;
+                wait(&b_staged[b], (g >> 1) & 1);
+                // w P buffer b was last read by the residual of chunk g - 2
+                if (g >= 2) wait(&b_res[b], ((g >> 1) & 1) ^ 1);
+                const float2 *B2 = s_Bst + b * NBST;
+                const float *wh = s_wst + b * 2 * CI, *wl = wh + CI;
+                float2 *WP2 = s_WP + b * WPBUF + warp * CI * G * PPT;
+
+                // pointwise (this warp's points, one ECM point per lane):
+                // F_i, law, w P_i (double-float), W_i = w_i A_i (float32)
+                {
+                    const int pl = lane % PPT, il = lane / PPT;
+                    const int p = p0 + pl;
+                    bool live = (s_flag[p] == ST_OK) && (i0 + il < m);
+                    const int ph = s_ph[b * CI + il];
+                    float fi[G];
+                    float lnJk = 0.0f;
+                    if (live) {
+                        df F[G], P[G];
+                        const float2 *b2 = B2 + il * G * BP;
+                        const float2 *q2 = s_q2 + p * QP;
+                        dacc sacc[G];
+#pragma unroll
+                        for (int c = 0; c < G; ++c) sacc[c] = dacc{s_Uh[p * G + c], s_Ul[p * G + c]};
+#pragma unroll 4
+                        for (int j = 0; j < n; ++j) {
+                            const float2 qj = q2[j];
+#pragma unroll
+                            for (int c = 0; c < G; ++c) {
+                                const float2 bj = b2[c * BP + j];
+                                dacc_fma(sacc[c], bj.x, bj.y, qj.x, qj.y);
+                            }
+                        }
+#pragma unroll
+                        for (int c = 0; c < G; ++c) F[c] = dacc_get(sacc[c]);
+                        if (!nh_stress_df<D>(F, ph ? dmu1 : dmu0, ph ? dlam1 : dlam0, P, fi, lnJk)) {
+                            atomicCAS(&s_flag[p], ST_OK, ST_DETF);
+                            live = false;
+                        } else {
+                            const df w2{wh[il], wl[il]};
+#pragma unroll
+                            for (int c = 0; c < G; ++c) {
+                                const df wp = df_mul(w2, P[c]);
+                                WP2[(il * G + c) * PPT + pl] = make_float2(wp.hi, wp.lo);
+                            }
+                        }
+                    }
+                    float4 *Wt = reinterpret_cast<float4 *>(Ww + (il * PPT + pl) * G * G);
+                    if (live) {
+                        const float muk = ph ? kmu1 : kmu0, lam = ph ? klam1 : klam0;
+                        const float c3 = muk - lam * lnJk;
+                        const float wk = wh[il];
+#pragma unroll
+                        for (int c = 0; c < G; ++c) {
+                            float Ar[G];
+                            nh_tangent_row<D, float>(fi, lam, c3, muk, c, Ar);
+                            Wt[c] = make_float4(wk * Ar[0], wk * Ar[1], wk * Ar[2], wk * Ar[3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < G; ++c) {
+                            WP2[(il * G + c) * PPT + pl] = make_float2(0.0f, 0.0f);
+                            Wt[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&b_wp[b]);
+
+                // a5: per k-step, this warp builds its tile's A rows and issues
+                // its three MMAs (D_tile += Yhi Bhi + Yhi Blo + Ylo Bhi)
+                const int j = lane % NAR;  // row within the point
+                for (int ks = 0; ks < KSC; ++ks) {
+                    const uint32_t s = gstep + (uint32_t)(ch * KSC + ks);
+                    const int yb = s & 1;
+                    if (s >= 2) wait(&mbar[yb], ((s - 2) >> 1) & 1);
+                    float *Yh = yw + yb * 2048, *Yl = Yh + 1024;
+#pragma unroll
+                    for (int e = 0; e < EPS; ++e) {
+                        const int il = ks * EPS + e;
+                        float bx[G];
+#pragma unroll
+                        for (int d = 0; d < G; ++d) bx[d] = (j < n) ? B2[(il * G + d) * BP + j].x : ((j - n == d) ? 1.0f : 0.0f);
+                        const bool jin = j < na;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int rl = k * 32 + lane;  // row within the tile
+                            const int pl = rl / NAR;
+                            const float4 *Wt = reinterpret_cast<const float4 *>(Ww + (il * PPT + pl) * G * G);
+                            float y[G];
+#pragma unroll
+                            for (int c = 0; c < G; ++c) {
+                                const float4 wv = Wt[c];
+                                float v = wv.x * bx[0];
+                                v = __fmaf_rn(wv.y, bx[1], v);
+                                v = __fmaf_rn(wv.z, bx[2], v);
+                                v = __fmaf_rn(wv.w, bx[3], v);
+                                y[c] = jin ? v : 0.0f;
+                            }
+                            float hi[G], lo[G];
+#pragma unroll
+                            for (int c = 0; c < G; ++c) tc::split_tf32(y[c], hi[c], lo[c]);
+                            const int off2 = e * 512 + rl * 4;
+                            *reinterpret_cast<float4 *>(Yh + off2) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                            *reinterpret_cast<float4 *>(Yl + off2) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                        }
+                    }
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (ks == 0) {
+                            wait(&b_bx[b], (g >> 1) & 1);
+                            // the accumulators of the previous chunk were folded
+                            if (g >= 1) wait(b_fold, (g - 1) & 1);
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t ba = tc::smem_u32(s_BX + b * (PL::BXBUF / 4) + ks * 2 * (PL::BXPART / 4));
+                        const uint64_t bdh = tc::smem_desc(ba, 128, 256);
+                        const uint64_t bdl = tc::smem_desc(ba + (uint32_t)PL::BXPART, 128, 256);
+                        const uint64_t adh = tc::smem_desc(tc::smem_u32(Yh), 2048, 128);
+                        const uint64_t adl = tc::smem_desc(tc::smem_u32(Yl), 2048, 128);
+                        const uint32_t dt = tbase + warp * NN;
+                        // a chunk's first MMA starts the accumulator fresh in the
+                        // first two chunks of a tile; later it adds onto the
+                        // fold's compensation term
+                        tc::mma_tf32(dt, adh, bdh, idesc, (ks > 0 || ch >= 2) ? 1u : 0u);
+                        tc::mma_tf32(dt, adh, bdl, idesc, 1u);
+                        tc::mma_tf32(dt, adl, bdh, idesc, 1u);
+                        tc::mma_commit(&mbar[yb]);
+                        if (ks == KSC - 1) tc::mma_commit(&b_chunk[warp]);  // the whole chunk
+                    }
+                    __syncwarp();
+                }
+            }
+            tc::named_bar(0, NT);  // B
+            gc += (uint32_t)nch;
+            gstep += (uint32_t)(nch * KSC);
+            tc::named_bar(0, NT);  // C
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase_init, PL::TALLOC);
+    }
+}
+
+}  // namespace rverom

@@ -55,6 +55,7 @@ bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) |
 #define RV_WS(D, NA, TA, TB, NP, CI) &launch_ws<D, NA, TA, TB, NP, CI>
 #define RV_SYM(D, NA, TA, NP, CI, KT) &launch_cfg<D, NA, TA, TA, NP, CI, KT, false, true>
 #define RV_TC(D, NA, NP, CI) &launch_tc<D, NA, NP, CI>
+#define RV_TCWS(D, NA, NP, CI) &launch_tc_ws<D, NA, NP, CI>
 
 int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, CandInfo *info) {
     LaunchFn c[4] = {};
@@ -81,7 +82,7 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, C
         } else if (n <= 24) {
             add(RV_SYM(2, 28, 7, 24, 10, float), "simt-symmetric <2,28> 24 points x 10 ECM", 1);
             add(RV_FUSED(2, 28, 7, 7, 16, 16, float), "simt-fused <2,28> 16 points x 16 ECM", 1);
-            add(RV_WS(2, 28, 7, 7, 8, 16), "simt-warp-specialized <2,28> 8 points x 16 ECM", 1);
+            add(RV_TCWS(2, 28, 32, 8), "tcgen05-tf32x3 <2,28> 8 tile + 4 helper warps, 32 points x 8 ECM + per-thread condensation", 2);
             add(RV_TC(2, 28, 32, 8), "tcgen05-tf32x3 <2,28> 32 points x 8 ECM + per-thread condensation", 2);
         } else if (n <= 32) {
             add(RV_SYM(2, 36, 6, 12, 16, float), "simt-symmetric <2,36> 6x6 blocks, 12 points x 16 ECM", 1);

@@ -7,6 +7,7 @@
 #include "rom_core.cuh"
 #include "rom_ws.cuh"
 #include "rom_tc.cuh"
+#include "rom_tc_ws.cuh"
 
 struct rverom_s {
     int dim = 2;
@@ -81,6 +82,41 @@ cudaError_t launch_tc(const EvalArgs &a, int n_sm, int64_t max_points, cudaStrea
     if (!a.t.Bimg || a.t.img_nn != PL::NN || !a.cond) return cudaErrorInvalidValue;
     auto kern = eval_tc_kernel<D, NA, NP, CI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
+    if (e != cudaSuccess) return e;
+    auto ckern = condense_kernel<D, NA, CT, TPP>;
+    e = cudaFuncSetAttribute(ckern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP::bytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ckern, CT * TPP, CP::bytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int64_t tiles = (max_points + NP - 1) / NP;
+    int64_t grid = n_sm;
+    if (tiles < grid) grid = tiles;
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = (int)grid;
+    kern<<<(unsigned)grid, PL::NT, PL::bytes, st>>>(a);
+    int64_t cgrid = (max_points + CT - 1) / CT, cmax = (int64_t)n_sm * occ;
+    if (cgrid > cmax) cgrid = cmax;
+    if (cgrid < 1) cgrid = 1;
+    ckern<<<(unsigned)cgrid, CT * TPP, CP::bytes, st>>>(a);
+    return cudaGetLastError();
+}
+// warp-specialized tensor-core kernel (8 tile warps, 4 helper warps) and the
+// same condensation kernel; refuses to launch if the compiled register count
+// differs from the allocation its in-kernel register split assumes
+template <int D, int NA, int NP, int CI>
+cudaError_t launch_tc_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
+    using PL = TcWsPlan<D, NA, NP, CI>;
+    constexpr int CT = 32, TPP = 8;
+    using CP = CondPlan<D, NA, CT, TPP>;
+    if (!a.t.Bimg || a.t.img_nn != PL::NN || !a.cond) return cudaErrorInvalidValue;
+    auto kern = eval_tc_ws_kernel<D, NA, NP, CI>;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != PL::REGS_LAUNCH) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
     if (e != cudaSuccess) return e;
     auto ckern = condense_kernel<D, NA, CT, TPP>;
     e = cudaFuncSetAttribute(ckern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP::bytes);
