@@ -52,11 +52,12 @@ WORKLOADS = {
 }
 
 # DRAM traffic per launch of the evaluation kernel from one ncu capture of
-# this workload (profiles/eval_tc_kernel_c2_full.md for the mixed form, whose
-# autotuned kernel is the tensor-core one; profiles/eval_kernel_c2_fp64_full.md);
+# this workload (profiles/eval_tc_ws_kernel_c2_full.md for the mixed form, whose
+# autotuned kernel is the warp-specialized tensor-core one;
+# profiles/eval_kernel_c2_fp64_full.md);
 # reported only for that workload and form, and to be refreshed whenever the
 # kernel changes.
-PROFILED_TRAFFIC = {('c2', 'mixed'): 17235968, ('c2', 'fp64'): 17142784}
+PROFILED_TRAFFIC = {('c2', 'mixed'): 17207552, ('c2', 'fp64'): 17142784}
 
 # algorithmic work per evaluation (FP64 FLOP of kinematics + residual + law,
 # symmetric-half tangent contraction FLOP), per ROM type
