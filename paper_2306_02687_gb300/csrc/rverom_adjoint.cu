@@ -61,7 +61,7 @@ extern "C" int rve_rom_adjoint(rverom_t h, int64_t n_points, const int32_t *type
             a.offset = h->bucket_small + (RVEROM_MAX_TYPES + 1) + t;
         }
         int grid = 0;
-        cudaError_t e = dispatch_eval<true>(h->dim, a.t.n, false, a, h->n_sm, n_points, st, &grid);
+        cudaError_t e = dispatch_adjoint(h->dim, a.t.n, a, h->n_sm, n_points, st, &grid);
         if (e != cudaSuccess || grid > h->partials_cap) return RVEROM_ERR_CUDA;
         k_theta_reduce<<<1, 32, 0, st>>>(h->partials, grid, gTheta + 4 * t);
         if (cudaGetLastError() != cudaSuccess) return RVEROM_ERR_CUDA;

@@ -157,7 +157,7 @@ extern "C" int rve_rom_adjoint_static(rverom_t h, int64_t n_points, const int32_
             a.offset = offsets + t;
         }
         int grid = 0;
-        cudaError_t e = dispatch_eval<true>(h->dim, a.t.n, false, a, h->n_sm, n_points, st, &grid);
+        cudaError_t e = dispatch_adjoint(h->dim, a.t.n, a, h->n_sm, n_points, st, &grid);
         if (e != cudaSuccess || grid > RVEROM_STATIC_MAX_CTAS) return RVEROM_ERR_CUDA;
         k_reduce<<<1, 32, 0, st>>>(partials, grid, gTheta + 4 * t);
         if (cudaGetLastError() != cudaSuccess) return RVEROM_ERR_CUDA;

@@ -139,35 +139,17 @@ cudaError_t launch_tc_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaSt
 }
 int tc_record_words(int dim, int n);
 
-// Tile configuration per (dimension, n~ bucket, precision).
-template <bool ADJ>
-cudaError_t dispatch_eval(int dim, int n, bool mixed, const EvalArgs &a, int n_sm, int64_t max_points,
-                          cudaStream_t st, int *grid_out) {
+// Tile configuration of the adjoint (float64 form) per (dimension, n~ bucket).
+inline cudaError_t dispatch_adjoint(int dim, int n, const EvalArgs &a, int n_sm, int64_t max_points,
+                                    cudaStream_t st, int *grid_out) {
     if (dim == 2) {
-        if (mixed && !ADJ) {
-            if (n <= 12) return launch_ws<2, 16, 4, 4, 8, 16>(a, n_sm, max_points, st, grid_out);
-            if (n <= 16) return launch_ws<2, 20, 5, 5, 8, 16>(a, n_sm, max_points, st, grid_out);
-            if (n <= 24) return launch_ws<2, 28, 7, 7, 8, 16>(a, n_sm, max_points, st, grid_out);
-        }
-        if (mixed) {
-            if (n <= 12) return launch_cfg<2, 16, 4, 4, 16, 16, float, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 16) return launch_cfg<2, 20, 5, 5, 16, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 24) return launch_cfg<2, 28, 7, 7, 16, 16, float, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 32) return launch_cfg<2, 36, 9, 9, 16, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 64) return launch_cfg<2, 72, 9, 9, 4, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
-        } else {
-            if (n <= 12) return launch_cfg<2, 16, 4, 4, 16, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 16) return launch_cfg<2, 20, 5, 5, 16, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 24) return launch_cfg<2, 28, 7, 7, 8, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 32) return launch_cfg<2, 36, 9, 9, 8, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
-            if (n <= 64) return launch_cfg<2, 72, 9, 9, 2, 8, double, ADJ>(a, n_sm, max_points, st, grid_out);
-        }
+        if (n <= 12) return launch_cfg<2, 16, 4, 4, 16, 8, double, true>(a, n_sm, max_points, st, grid_out);
+        if (n <= 16) return launch_cfg<2, 20, 5, 5, 16, 8, double, true>(a, n_sm, max_points, st, grid_out);
+        if (n <= 24) return launch_cfg<2, 28, 7, 7, 8, 8, double, true>(a, n_sm, max_points, st, grid_out);
+        if (n <= 32) return launch_cfg<2, 36, 9, 9, 8, 8, double, true>(a, n_sm, max_points, st, grid_out);
+        if (n <= 64) return launch_cfg<2, 72, 9, 9, 2, 8, double, true>(a, n_sm, max_points, st, grid_out);
     } else if (dim == 3) {
-        if (mixed) {
-            if (n <= 47) return launch_cfg<3, 56, 7, 7, 4, 8, float, ADJ>(a, n_sm, max_points, st, grid_out);
-        } else {
-            if (n <= 47) return launch_cfg<3, 56, 7, 7, 2, 4, double, ADJ>(a, n_sm, max_points, st, grid_out);
-        }
+        if (n <= 47) return launch_cfg<3, 56, 7, 7, 2, 4, double, true>(a, n_sm, max_points, st, grid_out);
     }
     return cudaErrorInvalidValue;
 }
