@@ -24,9 +24,9 @@
 //   fold       accumulators of the last chunk folded (accumulators free)
 // Registers: the block is launched with 168 per thread (384 threads); tile
 // warps raise theirs to 184 and helper warps lower theirs to 136
-// (8 x 32 x 184 + 4 x 32 x 136 = 384 x 168; the fold and the residual of all
-// points need more registers than the law of one point per lane); the launcher
-// checks the compiled count.
+// (8 x 32 x 184 + 4 x 32 x 136 = 384 x 168; with fewer registers the helpers'
+// fold and residual spill); the launcher checks the compiled count, since a
+// split that does not add up to the launch allocation would block forever.
 #pragma once
 
 #include "rom_tc.cuh"
@@ -152,10 +152,6 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    // Each role runs its own copy of the tile loop right after its register
-    // reallocation (so that the compiler sees one register budget per role);
-    // the CTA-wide barriers (id 0) of the two copies pair up: A after the
-    // polar split and micro update, B after the chunks, C after the records.
     // bounded wait; after the first timeout no wait blocks any more (the
     // tile's points are then marked ST_TIMEOUT)
     auto wait = [&](uint64_t *bar, uint32_t parity) {
@@ -187,6 +183,10 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
     };
 
     const uint32_t tbase_init = *s_slot;
+    // Each role runs its own copy of the tile loop right after its register
+    // reallocation (so that the compiler sees one register budget per role);
+    // the CTA-wide barriers (id 0) of the two copies pair up: A after the
+    // polar split and micro update, B after the chunks, C after the records.
     if (helper) {
         // ===================== helper warps =====================================
         tc::regs_dec<PL::REGS_HELP>();
