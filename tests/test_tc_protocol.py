@@ -1,0 +1,227 @@
+"""Hand-off protocol of the warp-specialized tensor-core kernel
+(csrc/rom_tc_ws.cuh), checked on the CPU under random schedules.
+
+The kernel's roles (8 tile warps, 4 helper warps, the asynchronous MMA and
+copy engines) are modelled as coroutines that advance one step at a time in a
+random order; MMAs of one warp complete in issue order but late, copies land
+late.  mbarriers follow the parity rule of `mbarrier.try_wait.parity`: a wait
+for parity p returns once the number of completed phases has the other
+parity, so it is well defined only for the current phase and the one before
+it.  Every data hazard the barriers guard is asserted:
+  - a fold reads the accumulators of a chunk before its MMAs completed, or
+    while MMAs of the next chunk run;
+  - MMAs of the next chunk start before all four lane quarters were folded;
+  - the residual reads w P or the tables before they were written / landed;
+  - a w P buffer, a staging buffer or a B-operand image is overwritten while
+    a reader may still use it; an A buffer is rewritten while MMAs read it;
+  - nothing makes progress (a wait that never returns).
+Two fold waits that are wrong pin the model's sensitivity: waiting for the
+last k-step's commit on a per-buffer barrier (two phases per chunk) lets the
+fold run early, and waiting for its two phases in turn blocks for good.
+"""
+import random
+
+import pytest
+
+NW, NH, KSC = 8, 4, 4
+
+
+class Barrier:
+    def __init__(self, count):
+        self.count, self.pending, self.phases = count, count, 0
+
+    def arrive(self):
+        self.pending -= 1
+        assert self.pending >= 0
+        if self.pending == 0:
+            self.phases += 1
+            self.pending = self.count
+
+    def passed(self, parity):
+        return (self.phases & 1) != parity
+
+
+class NamedBarrier:
+    def __init__(self, count):
+        self.count, self.arrived, self.generation = count, 0, 0
+
+
+class Hazard(AssertionError):
+    pass
+
+
+def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
+    rng = random.Random(seed)
+    bx = [Barrier(1), Barrier(1)]
+    commit = [[Barrier(1), Barrier(1)] for _ in range(NW)]
+    chunk = [Barrier(1) for _ in range(NW)]
+    staged = [Barrier(NH), Barrier(NH)]   # one arrival per helper warp's copies
+    wp = [Barrier(NW), Barrier(NW)]
+    res = [Barrier(NH), Barrier(NH)]
+    fold = Barrier(NH)
+    named = {0: NamedBarrier(NW + NH), 1: NamedBarrier(NH), 2: NamedBarrier(NW)}
+    events = []        # (time, action) of the asynchronous engines
+    last_mma = {}      # per warp: completion time of its latest MMA group
+    now = [0]
+    mma_done, mma_issued, folded = set(), set(), {}
+    wp_written, res_done, landed, readers, y_busy = {}, {}, set(), {}, {}
+
+    def check(cond, what):
+        if not cond:
+            raise Hazard(what)
+
+    def later(action, warp=None):
+        t = now[0] + rng.randint(1, 30)
+        if warp is not None:                 # one warp's MMAs complete in order
+            t = max(t, last_mma.get(warp, 0) + 1)
+            last_mma[warp] = t
+        events.append((t, action))
+
+    def wait(bar, parity):
+        while not bar.passed(parity):
+            yield
+
+    def sync(i):
+        nb = named[i]
+        gen = nb.generation
+        nb.arrived += 1
+        if nb.arrived == nb.count:
+            nb.arrived, nb.generation = 0, gen + 1
+        while nb.generation == gen:
+            yield
+
+    def stage(g):
+        b = g & 1
+        check(readers.get(g - 2, 0) == 0, 'tables of chunk %d overwritten while read' % (g - 2))
+        if g >= 2:
+            check(all((w, g - 2) in mma_done for w in range(NW)), 'B image of chunk %d overwritten' % (g - 2))
+
+        def land():
+            landed.add(g)
+            for _ in range(NH):
+                staged[b].arrive()
+        later(land)
+        later(bx[b].arrive)
+
+    def helper(h):
+        gc = gs = 0
+        for _ in range(n_tiles):
+            if h == 0:
+                stage(gc)
+                if nch > 1:
+                    stage(gc + 1)
+            yield from sync(0)
+            for ch in range(nch):
+                g = gc + ch
+                b = g & 1
+                sl = gs + ch * KSC + KSC - 1
+                for w in range(NW):
+                    if fold_wait == 'chunk':
+                        yield from wait(chunk[w], g & 1)
+                    elif fold_wait == 'buffer':
+                        yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+                    else:  # both phases of the buffer barrier in turn
+                        yield from wait(commit[w][sl & 1], ((sl >> 1) & 1) ^ 1)
+                        yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+                for w in range(NW):
+                    check((w, g) in mma_done, 'fold of chunk %d before its MMAs completed' % g)
+                    check((w, g + 1) not in mma_issued, 'fold of chunk %d while chunk %d runs' % (g, g + 1))
+                    folded.setdefault((w, g), set()).add(h)
+                    yield
+                fold.arrive()
+                yield from wait(wp[b], (g >> 1) & 1)
+                yield from wait(staged[b], (g >> 1) & 1)
+                check(len(wp_written.get(g, ())) == NW, 'residual of chunk %d before w P' % g)
+                check(g in landed, 'residual of chunk %d before its tables' % g)
+                readers[g] = readers.get(g, 0) + 1
+                yield
+                readers[g] -= 1
+                res_done.setdefault(g, set()).add(h)
+                res[b].arrive()
+                if ch + 2 < nch:
+                    yield from sync(1)
+                    if h == 0:
+                        stage(g + 2)
+            yield from sync(0)
+            gc += nch
+            gs += nch * KSC
+            yield from sync(0)
+
+    def tile(w):
+        gc = gs = 0
+        for _ in range(n_tiles):
+            yield from sync(2)
+            yield from sync(0)
+            for ch in range(nch):
+                g = gc + ch
+                b = g & 1
+                yield from wait(staged[b], (g >> 1) & 1)
+                if g >= 2:
+                    yield from wait(res[b], ((g >> 1) & 1) ^ 1)
+                check(g in landed, 'law of chunk %d before its tables' % g)
+                check(g < 2 or len(res_done.get(g - 2, ())) == NH, 'w P of chunk %d overwritten' % (g - 2))
+                readers[g] = readers.get(g, 0) + 1
+                wp_written.setdefault(g, set()).add(w)
+                wp[b].arrive()
+                for ks in range(KSC):
+                    s = gs + ch * KSC + ks
+                    yb = s & 1
+                    if s >= 2:
+                        yield from wait(commit[w][yb], ((s - 2) >> 1) & 1)
+                    check(y_busy.get((w, yb), 0) == 0, 'A buffer rewritten while MMAs read it')
+                    yield
+                    if ks == 0:
+                        yield from wait(bx[b], (g >> 1) & 1)
+                        if g >= 1:
+                            yield from wait(fold, (g - 1) & 1)
+                            check(len(folded.get((w, g - 1), ())) == NH, 'MMAs of chunk %d before the fold' % g)
+                    mma_issued.add((w, g))
+                    y_busy[(w, yb)] = y_busy.get((w, yb), 0) + 1
+                    last = ks == KSC - 1
+
+                    def complete(w=w, yb=yb, g=g, last=last):
+                        y_busy[(w, yb)] -= 1
+                        commit[w][yb].arrive()
+                        if last:
+                            mma_done.add((w, g))
+                            chunk[w].arrive()
+                    later(complete, warp=w)
+                readers[g] -= 1
+            yield from sync(0)
+            gc += nch
+            gs += nch * KSC
+            yield from sync(0)
+
+    agents = [helper(h) for h in range(NH)] + [tile(w) for w in range(NW)]
+    alive = list(range(len(agents)))
+    steps = 0
+    while alive:
+        steps += 1
+        check(steps < max_steps, 'no progress')
+        now[0] += 1
+        due = [e for e in events if e[0] <= now[0]]
+        for e in due:
+            events.remove(e)
+            e[1]()
+        i = rng.choice(alive)
+        try:
+            next(agents[i])
+        except StopIteration:
+            alive.remove(i)
+
+
+@pytest.mark.parametrize('seed', range(40))
+def test_protocol_is_hazard_free(seed):
+    run_schedule(seed, n_tiles=1 + seed % 3, nch=1 + (seed // 3) % 6)
+
+
+@pytest.mark.parametrize('variant, what', [('buffer', 'before its MMAs completed'), ('two-phase', 'no progress')])
+def test_wrong_fold_waits_are_caught(variant, what):
+    hits = 0
+    for seed in range(6):
+        try:
+            run_schedule(seed, n_tiles=2, nch=4, fold_wait=variant, max_steps=60_000)
+        except Hazard as e:
+            assert what in str(e)
+            hits += 1
+    assert hits > 0
