@@ -43,7 +43,7 @@ extern "C" {
 #define RVEROM_STATUS_DETF_NONPOS 1 /* det F <= 0 at some ECM point */
 #define RVEROM_STATUS_NONSPD_K 2    /* reduced stiffness not positive definite */
 #define RVEROM_STATUS_NONFINITE 3   /* NaN/Inf in the input or the reduced system */
-#define RVEROM_STATUS_TIMEOUT 5     /* a bounded internal wait of the tensor-core kernel ran out; the
+#define RVEROM_STATUS_TIMEOUT 5     /* a bounded internal wait of a tensor-core kernel ran out; the
                                        point's outputs are not valid (4 is the host drivers' NOT_CONVERGED) */
 
 #define RVEROM_FP64 0  /* every step in native float64 */
