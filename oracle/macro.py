@@ -135,7 +135,7 @@ def driver(problem, roms, types, n_steps, scheme='monolithic', tol=1e-10, maxit=
     d, nip = mesh.d, mesh.n_ip
     mu_m = roms[0].moduli[0, 0]
     state = [reduced.zero_state(roms[types[a]]) for a in range(nip)]
-    from . import polar as pol, rve as rvemod
+    from . import rve as rvemod
     for a in range(nip):
         state[a]['Uprev'] = rvemod.to_voigt(np.eye(d))
     u = np.zeros((mesh.n_nodes, d))

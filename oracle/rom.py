@@ -29,7 +29,7 @@ Readings where the paper is garbled or silent:
 import numpy as np
 import scipy.optimize as spo
 
-from . import reduced, rve as rvemod
+from . import reduced
 
 
 def snapshots(model, paths):

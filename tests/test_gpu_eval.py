@@ -6,7 +6,7 @@ import torch
 
 import synthetic as syn
 from conftest import rom_path
-from oracle import reduced, polar, rve
+from oracle import reduced, polar
 
 pytestmark = pytest.mark.gpu
 

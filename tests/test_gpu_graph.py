@@ -1,7 +1,6 @@
 """A monolithic Newton iteration (macro gradient, batched RVE evaluation,
 assembly, convergence norms) captured once in a CUDA graph and replayed
 gives the same results as eager launches."""
-import numpy as np
 import pytest
 import torch
 

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle import law, rve, polar
+from oracle import law, rve
 
 MU, KA = law.mu_kappa_from_E_nu(1.0, 0.3)
 MOD = [[MU, KA], [10 * MU, 10 * KA]]
