@@ -123,9 +123,9 @@ int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *type, const 
 /* Autotuner of the evaluation kernels: for every RVE type of the handle,
  * time each compiled tile configuration (SIMT or tcgen05 tensor-core
  * kernels; points per CTA, ECM points per chunk, warp roles) of the given
- * precision on
- * a synthetic batch of n_sample points (seeded small stretches, fresh state;
- * device memory for it is allocated and freed here), keep the fastest for
+ * precision on a synthetic batch of n_sample points (seeded small
+ * stretches, fresh state; device memory for it is allocated and freed
+ * here), keep the fastest for
  * rve_rom_eval_batch, and optionally report the best-of-2 times in
  * ms_out [n_types][RVEROM_MAX_CANDIDATES] (host; -1 for unused slots).
  * Synchronous.  Without tuning, configuration 0 of each list is used. */
