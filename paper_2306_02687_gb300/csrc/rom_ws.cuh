@@ -108,7 +108,6 @@ __global__ void __launch_bounds__(WsPlan<D, NA, TA, TB, NP, CI>::NT, 1) eval_ws_
     const int tid = threadIdx.x;
     const bool producer = tid < NPW;
     const int n = a.t.n, m = a.t.m;
-    const int na = n + G;
     const int nch = (m + CI - 1) / CI;
     const int64_t count = a.count ? (int64_t)(*a.count) : a.n_points;
     const int32_t *perm = a.perm ? a.perm + (a.offset ? *a.offset : 0) : nullptr;
