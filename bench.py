@@ -7,8 +7,13 @@ static condensation, rotation back) -> macro element assembly of R and K ->
 convergence scalars.  The metric is RVE evaluations per second (one
 evaluation = one macro point in one Newton iteration).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1..c5]
                   [--precision mixed|fp64] [--impl ours|reference]
+                  [--candidate I] [--no-cpu-baseline]
+
+--candidate pins one compiled kernel configuration instead of the
+autotuner's pick (as named by rve_rom_kernel_info); --no-cpu-baseline skips
+the timed oracle sample.
 
 Default workload c2: 2D plane strain, 48x48 Q4 RVE with 4 inclusions, 24
 modes, 200 ECM points, plate with a central hole (O-grid 4 x 32 x 32 Q4,
