@@ -18,6 +18,9 @@ it.  Every data hazard the barriers guard is asserted:
 Two fold waits that are wrong pin the model's sensitivity: waiting for the
 last k-step's commit on a per-buffer barrier (two phases per chunk) lets the
 fold run early, and waiting for its two phases in turn blocks for good.
+The single-role kernel (csrc/rom_tc.cuh: 8 warps, a CTA barrier per chunk)
+is modelled too; its earlier per-buffer fold wait passes early whenever a
+warp is two k-steps behind, which random schedules reach.
 """
 import random
 
@@ -223,5 +226,107 @@ def test_wrong_fold_waits_are_caught(variant, what):
             run_schedule(seed, n_tiles=2, nch=4, fold_wait=variant, max_steps=60_000)
         except Hazard as e:
             assert what in str(e)
+            hits += 1
+    assert hits > 0
+
+
+def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
+    """Protocol of the single-role kernel (csrc/rom_tc.cuh): 8 warps, each
+    issuing its own tile's MMAs per k-step and folding one lane quarter of
+    every tile after the chunk, then a CTA barrier; returns nothing, raises
+    Hazard."""
+    rng = random.Random(seed)
+    commit = [[Barrier(1), Barrier(1)] for _ in range(NW)]
+    chunk = [Barrier(1) for _ in range(NW)]
+    cta = NamedBarrier(NW)
+    events, last_mma, now = [], {}, [0]
+    mma_done, folds = set(), {}
+
+    def check(cond, what):
+        if not cond:
+            raise Hazard(what)
+
+    def later(action, warp):
+        t = max(now[0] + rng.randint(1, 30), last_mma.get(warp, 0) + 1)
+        last_mma[warp] = t
+        events.append((t, action))
+
+    def wait(bar, parity):
+        while not bar.passed(parity):
+            yield
+
+    def sync():
+        gen = cta.generation
+        cta.arrived += 1
+        if cta.arrived == cta.count:
+            cta.arrived, cta.generation = 0, gen + 1
+        while cta.generation == gen:
+            yield
+
+    def warp(w):
+        gstep = gchunk = 0
+        for _ in range(n_tiles):
+            for ch in range(nch):
+                for ks in range(KSC):
+                    s = gstep + ks
+                    if s >= 2:
+                        yield from wait(commit[w][s & 1], ((s - 2) >> 1) & 1)
+                    yield
+                    check(all(folds.get((t, gchunk - 1), 0) == NW for t in range(NW)) or ch == 0 and gchunk == 0,
+                          'MMAs before the fold of the previous chunk')
+                    last = ks == KSC - 1
+
+                    def complete(w=w, s=s, g=gchunk, last=last):
+                        commit[w][s & 1].arrive()
+                        if last:
+                            mma_done.add((w, g))
+                            chunk[w].arrive()
+                    later(complete, w)
+                gstep += KSC
+                sl = gstep - 1
+                for w2 in range(NW):
+                    if fold_wait == 'chunk':
+                        yield from wait(chunk[w2], gchunk & 1)
+                    else:
+                        yield from wait(commit[w2][sl & 1], (sl >> 1) & 1)
+                for t in range(NW):
+                    check((t, gchunk) in mma_done, 'fold of chunk %d before its MMAs completed' % gchunk)
+                    folds[(t, gchunk)] = folds.get((t, gchunk), 0) + 1
+                    yield
+                yield from sync()
+                gchunk += 1
+
+    agents = [warp(w) for w in range(NW)]
+    alive = list(range(NW))
+    steps = 0
+    while alive:
+        steps += 1
+        check(steps < max_steps, 'no progress')
+        now[0] += 1
+        due = [e for e in events if e[0] <= now[0]]
+        for e in due:
+            events.remove(e)
+            e[1]()
+        i = rng.choice(alive)
+        try:
+            next(agents[i])
+        except StopIteration:
+            alive.remove(i)
+
+
+@pytest.mark.parametrize('seed', range(20))
+def test_single_role_protocol_is_hazard_free(seed):
+    run_single_role(seed, n_tiles=1 + seed % 2, nch=1 + seed % 5)
+
+
+def test_single_role_buffer_wait_is_caught():
+    # waiting for the last k-step's commit on its per-buffer barrier passes
+    # early whenever another warp is two k-steps behind
+    hits = 0
+    for seed in range(30):
+        try:
+            run_single_role(seed, n_tiles=1, nch=4, fold_wait='buffer')
+        except Hazard as e:
+            assert 'before its MMAs completed' in str(e)
             hits += 1
     assert hits > 0
