@@ -9,11 +9,13 @@ evaluation = one macro point in one Newton iteration).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1..c5]
                   [--precision mixed|fp64] [--impl ours|reference]
-                  [--candidate I] [--no-cpu-baseline]
+                  [--candidate I] [--no-cpu-baseline] [--no-oracle-check]
 
 --candidate pins one compiled kernel configuration instead of the
 autotuner's pick (as named by rve_rom_kernel_info); --no-cpu-baseline skips
-the timed oracle sample.
+the timed oracle sample; --no-oracle-check skips the accuracy check of the
+timed form against the float64 oracle on 256 sampled points (mid-Newton
+states the oracle converged), reported per output in accuracy_vs_oracle.
 
 Default workload c2: 2D plane strain, 48x48 Q4 RVE with 4 inclusions, 24
 modes, 200 ECM points, plate with a central hole (O-grid 4 x 32 x 32 Q4,
@@ -57,11 +59,9 @@ WORKLOADS = {
 }
 
 # DRAM traffic per launch of the evaluation kernel from one ncu capture of
-# this workload (profiles/eval_tc_ws_kernel_c2_full.md for the mixed form, whose
-# autotuned kernel is the warp-specialized tensor-core one;
-# profiles/eval_kernel_c2_fp64_full.md);
-# reported only for that workload and form, and to be refreshed whenever the
-# kernel changes.
+# this workload (the warp-specialized tensor-core kernel the autotuner picks
+# for the mixed form, and the float64 kernel); reported only for that
+# workload and form, and to be refreshed whenever the kernel changes.
 PROFILED_TRAFFIC = {('c2', 'mixed'): 17207552, ('c2', 'fp64'): 17142784}
 
 # algorithmic work per evaluation (FP64 FLOP of kinematics + residual + law,
@@ -188,6 +188,52 @@ def oracle_rate(rom_paths, types, F, q, s, S, U, budget_s, max_points=None):
             return cnt / el, cnt, el
 
 
+def oracle_accuracy(rom_paths, types_np, F_or, sel, seed):
+    """Oracle inputs and outputs at the sampled points: a mid-Newton state per
+    point (micro state converged by the oracle at a nearby Fbar, the stored
+    s, S, U_prev of that evaluation, q perturbed by 1e-3 of its size), then
+    one oracle evaluation at the workload's Fbar.  Inputs come from the
+    oracle and the seeded generators only."""
+    from oracle import reduced
+    roms = [reduced.Rom.load(p) for p in rom_paths]
+    states, outs = [], []
+    for k, a in enumerate(sel):
+        r = roms[types_np[a]]
+        F1 = F_or[a]
+        F0 = F1 - syn.perturbation(seed + 2 * k, F1.shape, 2e-3)
+        o, _ = reduced.converge_point(r, F0)
+        q = o['q'] + syn.perturbation(seed + 2 * k + 1, r.n, 1e-3 * np.abs(o['q']).max())
+        st = dict(q=q, s=o['s'], S=o['S'], Uprev=o['Uprev'])
+        states.append(st)
+        outs.append(reduced.eval_point(r, F1, **st))
+    return states, outs
+
+
+def accuracy_report(g, outs, sel, types_np, rom_n):
+    """Largest relative error per output over the sampled points (P, dPdF
+    relative to the point's largest entry; s, S, q likewise; rnorm relative
+    to itself)."""
+    def rel(x, y):
+        return float(np.abs(x - y).max() / max(np.abs(y).max(), 1e-300))
+    errs = dict(Pbar=0.0, dPdF=0.0, s=0.0, S=0.0, q=0.0, rnorm=0.0)
+    bad = 0
+    for k, (a, o) in enumerate(zip(sel, outs)):
+        if g['status'][k] != 0 or o['status'] != 0:
+            bad += 1
+            continue
+        n = rom_n[types_np[a]]
+        errs['Pbar'] = max(errs['Pbar'], rel(g['Pbar'][k], o['Pbar'].ravel()))
+        errs['dPdF'] = max(errs['dPdF'], rel(g['dPdF'][k], o['dPdF']))
+        errs['s'] = max(errs['s'], rel(g['s'][k][:n], o['s']))
+        errs['S'] = max(errs['S'], rel(g['S'][k][:n], o['S']))
+        errs['q'] = max(errs['q'], rel(g['q'][k][:n], o['q']))
+        errs['rnorm'] = max(errs['rnorm'], abs(g['rnorm'][k] - o['rnorm']) / max(o['rnorm'], 1e-300))
+    out = {k + '_rel_err_max': v for k, v in errs.items()}
+    out['points'] = len(sel)
+    out['failed_points'] = bad
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -197,6 +243,8 @@ def main():
     ap.add_argument('--precision', default='mixed', choices=['mixed', 'fp64'])
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-oracle-check', action='store_true',
+                    help='skip the per-output comparison with the float64 oracle on 256 sampled points')
     ap.add_argument('--candidate', type=int, default=-1,
                     help='force this forward kernel candidate (rve_rom_select_kernel) for every type and '
                          'precision after autotuning; -1 keeps the autotuner\'s choice')
@@ -326,6 +374,34 @@ def main():
     p_err = ((P1 - Pbar).abs().amax(dim=1) / pn).max().item()
     c_err = ((C1 - dPdF).abs().amax(dim=(1, 2)) / cn).max().item()
 
+    # accuracy of the timed form against the float64 oracle, per output, on
+    # 256 sampled points that carry oracle mid-Newton states (the workload's
+    # Fbar from the oracle's macro gradient of the same displacement field)
+    acc = None
+    if not args.no_oracle_check:
+        from oracle import macro as omacro
+        F_or = omacro.MacroMesh(X, conn).gradient(u_host)
+        sel = np.sort(syn.rng(syn.SEED_BASE + 800 + rank).choice(n, min(n, 256), replace=False))
+        states, outs = oracle_accuracy(rom_paths, types_np, F_or, sel, syn.SEED_BASE + 900 + 1000 * rank)
+        restore()
+        si = torch.tensor(sel, device=dev)
+        Fbar[si] = torch.tensor(F_or[sel].reshape(len(sel), d * d), device=dev)
+        for k, st in enumerate(states):
+            nk = len(st['q'])
+            for x, v in ((q, st['q']), (s, st['s']), (S, st['S'])):
+                x[sel[k]].zero_()
+                x[sel[k], :nk] = torch.tensor(v, device=dev)
+            U[sel[k]] = torch.tensor(st['Uprev'], device=dev)
+        rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types,
+                              precision=args.precision)
+        torch.cuda.synchronize()
+        g_acc = {k: v[si].cpu().numpy() for k, v in dict(Pbar=Pbar, dPdF=dPdF, s=s, S=S, q=q, rnorm=rnorm,
+                                                          status=status).items()}
+        acc = accuracy_report(g_acc, outs, sel, types_np, [r['B'].shape[2] for r in roms])
+        acc["gate"] = {"Pbar": 1e-8, "dPdF": 1e-5}
+        acc["meets_gate"] = bool(acc['failed_points'] == 0 and acc['Pbar_rel_err_max'] <= 1e-8
+                                 and acc['dPdF_rel_err_max'] <= 1e-5)
+
     # end to end through the public API: pinned host u in, R / K / norms out
     u_pin = torch.tensor(u_host).pin_memory()
     R_pin = torch.empty(mesh.n_dof, dtype=torch.float64).pin_memory()
@@ -450,7 +526,9 @@ def main():
         "clocks": clocks,
         "other_form": {"precision": other, "value": world * n / (ms_other * 1e-3), "ms_per_step": ms_other},
         "speedup_vs_fp64_form": (ms_other / ms_step) if args.precision == 'mixed' else 1.0,
-        "accuracy_vs_fp64_form": {"Pbar_rel_err_max": p_err, "dPdF_rel_err_max": c_err},
+        "accuracy_vs_fp64_form": {"Pbar_rel_err_max": p_err, "dPdF_rel_err_max": c_err,
+                                  "points": n, "note": "every point, against the GPU float64 form"},
+        "accuracy_vs_oracle": acc,
     }
     print(json.dumps(out))
     if dist:

@@ -128,6 +128,9 @@ int rve_rom_eval_batch(rverom_t h, int64_t n_points, const int32_t *type, const 
  * here), keep the fastest for
  * rve_rom_eval_batch, and optionally report the best-of-2 times in
  * ms_out [n_types][RVEROM_MAX_CANDIDATES] (host; -1 for unused slots).
+ * A candidate for which any point of the sample ends with a status other
+ * than RVEROM_STATUS_OK is never kept (its ms_out entry is -2); if no
+ * candidate of a type is valid, configuration 0 stays in use.
  * Synchronous.  Without tuning, configuration 0 of each list is used. */
 #define RVEROM_MAX_CANDIDATES 4
 int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample, float *ms_out, void *stream);

@@ -7,7 +7,7 @@ restatement of the method, written from the paper's equations.  Only the test
 suite, the smoke check and the benchmark's CPU-baseline leg may import it.  It
 shares no code with the CUDA path (paper_2306_02687_gb300/) and never imports
 it; the two meet only in the seeded generators of the `synthetic` module and in
-ROM files written by `oracle/make_roms.py`.
+ROM files written by `tests/golden/make_roms.py`.
 
 Modules
   law       compressible Neo-Hooke law (stand-in constitutive law; the paper

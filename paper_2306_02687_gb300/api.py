@@ -131,7 +131,8 @@ def rve_rom_set_moduli(h, type_id, moduli):
 def rve_rom_autotune(h, precision='mixed', n_sample=16384, stream=None):
     """Time the compiled tile configurations of every RVE type on a synthetic
     sample and keep the fastest; returns the times [n_types][candidates]
-    in ms (-1 where a type has fewer candidates)."""
+    in ms (-1 where a type has fewer candidates, -2 for a candidate rejected
+    because a point of the sample did not end with status OK)."""
     ms = np.zeros((h.n_types, 4), dtype=np.float32)
     _native.check(_native.lib().rve_rom_autotune(h.ptr, _PREC[precision], int(n_sample),
                                                  ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),

@@ -88,7 +88,8 @@ struct TcPlan {
     // A buffer, [2 + 2 NW + w] MMAs of a whole chunk of warp w; then TMEM
     // slot, error flag
     static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);
-    static constexpr size_t o_slot = o_bar + (2 + 3 * NW) * 8;
+    // mbarriers: bx[2], commit[NW][2], chunk[NW], drain
+    static constexpr size_t o_slot = o_bar + (3 + 3 * NW) * 8;
     static constexpr size_t bytes = tc_al(o_slot + 8);
     static_assert(bytes <= 227 * 1024, "shared memory");
 };
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     }
     if (tid == 0) {
         for (int b = 0; b < 2 + 3 * NW; ++b) tc::mbar_init(&s_bar[b], 1);
+        tc::mbar_init(&s_bar[2 + 3 * NW], NW);  // drain
         tc::mbar_init_fence();
         *s_err = 0;
     }
@@ -161,8 +163,9 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     tc::fence_after_sync();
     const uint32_t tbase = *s_slot;
     const uint32_t idesc = tc::idesc_tf32(128, NN);
-    // bounded wait; after the first timeout no wait blocks any more (the
-    // tile's points are then marked ST_TIMEOUT)
+    // bounded wait (tc::WAIT_LIMIT_NS); after the first timeout no wait
+    // blocks any more, no MMA or bulk copy is issued, and the tile's points
+    // are marked ST_TIMEOUT
     auto wait = [&](uint64_t *bar, uint32_t parity) {
         if (*s_err == 0 && !tc::mbar_wait(bar, parity)) *s_err = 1;
     };
@@ -185,7 +188,14 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         }
         cp_async_commit();
     };
-    auto stage_bulk = [&](int buf, int ch) {  // one thread
+    // bulk copy of the B-operand image of chunk ch (CTA-wide chunk index g)
+    // into buffer g & 1, by one thread; nothing is issued once a wait of the
+    // CTA has timed out
+    int64_t bx_last0 = -1, bx_last1 = -1;  // last chunk index copied into each buffer (thread 0)
+    auto stage_bulk = [&](uint32_t g, int ch) {
+        if (*s_err != 0) return;
+        const int buf = g & 1;
+        if (buf) bx_last1 = g; else bx_last0 = g;
         tc::mbar_arrive_expect_tx(&s_bar[buf], (uint32_t)PL::BXBUF);
         tc::bulk_g2s(s_BX + buf * (PL::BXBUF / 4), a.t.Bimg + (size_t)ch * (PL::BXBUF / 4), (uint32_t)PL::BXBUF,
                      &s_bar[buf]);
@@ -256,7 +266,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         df pudf{0.0f, 0.0f};
         // first chunk's tables
         stage_cp(gchunk & 1, 0);
-        if (tid == 0) stage_bulk(gchunk & 1, 0);
+        if (tid == 0) stage_bulk(gchunk, 0);
         cp_async_wait<0>();
         __syncthreads();
 
@@ -270,7 +280,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             // before the barrier that closed it
             if (ch + 1 < nch) {
                 stage_cp(buf ^ 1, i0 + CI);
-                if (tid == 0) stage_bulk(buf ^ 1, ch + 1);
+                if (tid == 0) stage_bulk(gchunk + 1, ch + 1);
             }
             const float2 *B2 = s_Bst + buf * NBST;
             const float *wh = s_wst + buf * 2 * CI, *wl = wh + CI;
@@ -375,8 +385,8 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 }
                 tc::fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) {
-                    if (ks == 0) wait(&s_bar[buf], (gchunk >> 1) & 1);
+                if (lane == 0 && ks == 0) wait(&s_bar[buf], (gchunk >> 1) & 1);
+                if (lane == 0 && *s_err == 0) {
                     tc::fence_after_sync();
                     const uint32_t ba = tc::smem_u32(s_BX + buf * (PL::BXBUF / 4) + ks * 2 * (PL::BXPART / 4));
                     const uint64_t bdh = tc::smem_desc(ba, 128, 256);
@@ -547,6 +557,18 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         }
         __syncthreads();
     }
+    // drain before TMEM is freed: every MMA this warp issued has completed
+    // (immediate unless a timeout skipped the fold waits), and the last bulk
+    // copy into each buffer has landed
+    if (lane == 0) {
+        tc::mma_commit(&s_bar[2 + 3 * NW]);
+        tc::mbar_wait(&s_bar[2 + 3 * NW], 0);
+    }
+    if (tid == 0) {
+        if (bx_last0 >= 0) tc::mbar_wait(&s_bar[0], (uint32_t)(bx_last0 >> 1) & 1);
+        if (bx_last1 >= 0) tc::mbar_wait(&s_bar[1], (uint32_t)(bx_last1 >> 1) & 1);
+    }
+    cp_async_wait<0>();
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {

@@ -22,6 +22,12 @@
 //   wp[b]      w_i P_i of a chunk written by every tile warp (buffer b)
 //   res[b]     residual of the chunk in buffer b done (w P buffer free)
 //   fold       accumulators of the last chunk folded (accumulators free)
+//   drain      every MMA of every tile warp completed (before TMEM is freed)
+// Every wait gives up after a bounded time (tc::WAIT_LIMIT_NS); after the
+// first timeout of a CTA no wait blocks any more, no further MMA or bulk copy
+// is issued, and the CTA's points are marked ST_TIMEOUT.  Before the CTA frees
+// its TMEM and exits, every tile warp waits (bounded) for the completion of
+// all MMAs it issued and the helpers for the copies they issued.
 // Registers: the block is launched with 168 per thread (384 threads); tile
 // warps raise theirs to 184 and helper warps lower theirs to 136
 // (8 x 32 x 184 + 4 x 32 x 136 = 384 x 168; with fewer registers the helpers'
@@ -83,8 +89,8 @@ struct TcWsPlan {
     static constexpr size_t o_Udf = tc_al(o_dU + (size_t)NP * NS * 8);
     static constexpr size_t o_flag = tc_al(o_Udf + 2 * (size_t)NP * G * 4);
     static constexpr size_t o_pidx = o_flag + NP * 4;
-    // mbarriers: bx[2], commit[NW][2], staged[2], wp[2], res[2], fold, chunk[NW]
-    static constexpr int NBAR = 2 + 2 * NW + 2 + 2 + 2 + 1 + NW;
+    // mbarriers: bx[2], commit[NW][2], staged[2], wp[2], res[2], fold, chunk[NW], drain
+    static constexpr int NBAR = 2 + 2 * NW + 2 + 2 + 2 + 1 + NW + 1;
     static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);
     static constexpr size_t o_slot = o_bar + NBAR * 8;
     static constexpr size_t bytes = tc_al(o_slot + 8);
@@ -117,6 +123,7 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + PL::o_bar);
     uint64_t *b_bx = s_bar, *b_commit = s_bar + 2, *b_staged = b_commit + 2 * NW;
     uint64_t *b_wp = b_staged + 2, *b_res = b_wp + 2, *b_fold = b_res + 2, *b_chunk = b_fold + 1;
+    uint64_t *b_drain = b_chunk + NW;
     uint32_t *s_slot = reinterpret_cast<uint32_t *>(smem + PL::o_slot);
     volatile int *s_err = reinterpret_cast<volatile int *>(smem + PL::o_slot + 4);
 
@@ -144,6 +151,7 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
         }
         tc::mbar_init(b_fold, NH);
         for (int w = 0; w < NW; ++w) tc::mbar_init(&b_chunk[w], 1);
+        tc::mbar_init(b_drain, NW);
         tc::mbar_init_fence();
         *s_err = 0;
     }
@@ -157,8 +165,11 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
     auto wait = [&](uint64_t *bar, uint32_t parity) {
         if (*s_err == 0 && !tc::mbar_wait(bar, parity)) *s_err = 1;
     };
-    // helper threads: tables of chunk ch (CTA-wide chunk index g) into buffer g & 1
+    // helper threads: tables of chunk ch (CTA-wide chunk index g) into buffer g & 1;
+    // nothing is issued once a wait of the CTA has timed out
+    int64_t bx_last0 = -1, bx_last1 = -1;  // last chunk index g bulk-copied into each buffer (issuing thread)
     auto stage = [&](uint32_t g, int ch) {
+        if (*s_err != 0) return;
         const int b = g & 1, i0s = ch * CI, ht = tid - NW * 32;
         float *b2 = reinterpret_cast<float *>(s_Bst + b * NBST);
         float *wh = s_wst + b * 2 * CI, *wl = wh + CI;
@@ -176,6 +187,7 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
         }
         tc::cp_async_mbar_arrive(&b_staged[b]);
         if (ht == 0) {
+            if (b) bx_last1 = g; else bx_last0 = g;
             tc::mbar_arrive_expect_tx(&b_bx[b], (uint32_t)PL::BXBUF);
             tc::bulk_g2s(s_BX + b * (PL::BXBUF / 4), a.t.Bimg + (size_t)ch * (PL::BXBUF / 4), (uint32_t)PL::BXBUF,
                          &b_bx[b]);
@@ -339,6 +351,12 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
             gc += (uint32_t)nch;
             gstep += (uint32_t)(nch * KSC);
             tc::named_bar(0, NT);  // C: records written before the next tile's a1
+        }
+        // drain: this thread's copies (normally all consumed already)
+        tc::cp_async_wait_all();
+        if (tid == NW * 32) {
+            if (bx_last0 >= 0) tc::mbar_wait(&b_bx[0], (uint32_t)(bx_last0 >> 1) & 1);
+            if (bx_last1 >= 0) tc::mbar_wait(&b_bx[1], (uint32_t)(bx_last1 >> 1) & 1);
         }
     } else {
         // ===================== tile warps =======================================
@@ -536,6 +554,8 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                             // the accumulators of the previous chunk were folded
                             if (g >= 1) wait(b_fold, (g - 1) & 1);
                         }
+                    }
+                    if (lane == 0 && *s_err == 0) {
                         tc::fence_after_sync();
                         const uint32_t ba = tc::smem_u32(s_BX + b * (PL::BXBUF / 4) + ks * 2 * (PL::BXPART / 4));
                         const uint64_t bdh = tc::smem_desc(ba, 128, 256);
@@ -560,6 +580,13 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
             gstep += (uint32_t)(nch * KSC);
             tc::named_bar(0, NT);  // C
         }
+        // drain: the completion of every MMA this warp issued (immediate
+        // unless a timeout skipped the fold waits), before TMEM is freed
+        if (lane == 0) {
+            tc::mma_commit(b_drain);
+            tc::mbar_wait(b_drain, 0);
+        }
+        __syncwarp();
     }
     tc::fence_before_sync();
     __syncthreads();

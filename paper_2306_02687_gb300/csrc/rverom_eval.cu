@@ -488,11 +488,12 @@ extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample,
     cudaEventCreate(&e1);
     int rc = RVEROM_OK;
     const int pi = precision == RVEROM_MIXED ? 1 : 0;
+    std::vector<int32_t> st_host((size_t)n);
     for (int t = 0; t < h->n_types && rc == RVEROM_OK; ++t) {
         LaunchFn cand[8];
         const int nc = forward_candidates(h->dim, h->types[t].n, precision == RVEROM_MIXED, cand, 8);
         float best = 1e30f;
-        int bi = 0;
+        int bi = -1;
         for (int c = 0; c < nc; ++c) {
             EvalArgs a = {};
             a.t = h->types[t];
@@ -510,6 +511,7 @@ extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample,
             a.status = status;
             a.cond = cond;
             float tbest = 1e30f;
+            bool valid = true;
             for (int rep = 0; rep < 3 && rc == RVEROM_OK; ++rep) {
                 k_tune_inputs<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(
                     n, h->dim, h->nmax, Fbar, q, s, S, U);
@@ -521,15 +523,26 @@ extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample,
                 if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
                     rc = RVEROM_ERR_CUDA;
                 if (rep > 0 && ms < tbest) tbest = ms;  // first repetition warms up
+                // a candidate that reports any non-OK status on the sample (a
+                // timed-out internal wait ends a kernel early and would time
+                // fastest) is rejected
+                if (rc == RVEROM_OK) {
+                    if (cudaMemcpy(st_host.data(), status, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+                        cudaSuccess)
+                        rc = RVEROM_ERR_CUDA;
+                    for (int64_t i = 0; i < n && valid; ++i) valid = st_host[(size_t)i] == RVEROM_STATUS_OK;
+                }
             }
-            if (ms_out) ms_out[t * RVEROM_MAX_CANDIDATES + c] = tbest;
-            if (tbest < best) {
+            if (ms_out) ms_out[t * RVEROM_MAX_CANDIDATES + c] = valid ? tbest : -2.0f;
+            if (valid && tbest < best) {
                 best = tbest;
                 bi = c;
             }
         }
         for (int c = nc; ms_out && c < RVEROM_MAX_CANDIDATES; ++c) ms_out[t * RVEROM_MAX_CANDIDATES + c] = -1.0f;
-        h->choice[t][pi] = bi;
+        // no valid candidate: keep the default configuration (its points
+        // report their status in rve_rom_eval_batch)
+        h->choice[t][pi] = bi >= 0 ? bi : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

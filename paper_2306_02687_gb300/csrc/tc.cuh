@@ -42,14 +42,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for the completion of the phase with the given parity.  Gives up after
-// `limit` polls (each poll blocks for at most a hardware-defined time slice)
-// and returns false; the caller records the failure and carries on without
-// touching the data the barrier guards.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = (1u << 22)) {
-    for (uint32_t it = 0; it < limit; ++it)
+// global nanosecond timer of the GPU
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Longest time a kernel waits on one mbarrier phase.  The longest legitimate
+// wait of the tensor-core kernels (a helper warp waiting for the slowest tile
+// warp's chunk) takes tens of microseconds, so 20 ms only ever expires when
+// the protocol is broken, and a broken kernel still ends within milliseconds.
+constexpr uint64_t WAIT_LIMIT_NS = 20ull * 1000ull * 1000ull;
+// Wait for the completion of the phase with the given parity.  Gives up once
+// `limit_ns` of global time have passed since the call and returns false; the
+// caller records the failure and carries on without touching the data the
+// barrier guards.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = WAIT_LIMIT_NS) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
 }
 
 // plain arrive (release semantics for this thread's earlier shared-memory writes)
@@ -61,6 +75,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+
+// wait until every cp.async issued so far by this thread has completed
+// (including those tracked only by cp.async.mbarrier.arrive)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ---- register reallocation between warpgroups -------------------------------
 // All four warps of a warpgroup execute the same call.  The per-thread counts

@@ -221,7 +221,8 @@ def test_nonspd_reduced_stiffness(precision):
 def test_full_size_2d_sampled():
     # 48x48 RVE / 24 modes / 200 ECM points at 16384 macro points (the
     # benchmark's launch configuration); 32 sampled points carry oracle
-    # mid-Newton states and are compared with the oracle one by one
+    # mid-Newton states and are compared with the oracle one by one, under
+    # the default candidate and under the autotuner's pick
     h, oroms = _handle(['c2'])
     n = 16384
     orom = oroms[0]
@@ -237,6 +238,13 @@ def test_full_size_2d_sampled():
     for precision, tol in (('fp64', TOL_FP64), ('mixed', TOL_MIXED)):
         g = run_gpu(h, F, q, s, S, U, precision)
         assert np.all(g['status'] == 0)
+        compare({k: v[idx] for k, v in g.items()}, outs, h.nmax, tol)
+        # the autotuner's pick (the benchmark's kernel) on the same batch
+        ms = rv.rve_rom_autotune(h, precision, n_sample=n)
+        assert np.all(ms[0][ms[0] != -1] > 0), ms      # no candidate rejected for a bad status
+        g = run_gpu(h, F, q, s, S, U, precision)
+        assert np.all(g['status'] == 0)
+        print(precision, 'autotuned:', rv.rve_rom_kernel_info(h, 0, precision)[0])
         compare({k: v[idx] for k, v in g.items()}, outs, h.nmax, tol)
 
 
@@ -334,20 +342,35 @@ def test_every_tile_configuration_matches_oracle(names):
         compare(run_gpu(h, F, q, s, S, U, precision, types=types), outs, h.nmax, tol)
 
 
-@pytest.mark.parametrize('name', ['c1', 'c2'])
-def test_tensor_core_kernel_many_tiles(name):
-    # the tcgen05 candidate (last in the list) over several tiles per CTA and
-    # a ragged tail: element-wise against the SIMT mixed kernel on every
-    # point, and against the oracle on sampled mid-Newton points
+def tensor_core_candidates(h, t=0):
+    """(index, name) of every tcgen05 candidate of type t (mixed form)."""
+    nc = rv.rve_rom_select_kernel(h, t, 'mixed')
+    names = [rv.rve_rom_kernel_info(h, t, 'mixed', c)[0] for c in range(nc)]
+    return [(c, nm) for c, nm in enumerate(names) if nm.startswith('tcgen05')]
+
+
+@pytest.mark.parametrize('name,kind', [('c1', 'single-role'), ('c2', 'single-role'), ('c2', 'warp-specialized')])
+def test_tensor_core_kernel_many_tiles(name, kind):
+    # each tcgen05 candidate, selected by name, in the launch configuration of
+    # the benchmark: a persistent grid of one CTA per SM working through at
+    # least 3 tiles of points each (the cross-tile phase bookkeeping of its
+    # mbarriers), with a ragged last tile.  Element-wise against the SIMT
+    # mixed kernel on every point, and against the oracle on 40 sampled
+    # mid-Newton points at the mixed-form gate.
     import os
+    import re
     if not os.path.exists(rom_path(name)):
         pytest.skip('ROM file not generated')
     h, oroms = _handle([name])
     orom = oroms[0]
-    nc = rv.rve_rom_select_kernel(h, 0, 'mixed')
-    assert nc == 4
-    n = 2 * 152 * 64 + 13
-    idx = np.sort(syn.rng(11).choice(n, 24, replace=False))
+    cands = [(c, nm) for c, nm in tensor_core_candidates(h) if ('helper' in nm) == (kind == 'warp-specialized')]
+    assert len(cands) == 1, cands
+    cand, cname = cands[0]
+    n_pts_cta = int(re.search(r'(\d+) points', cname).group(1))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 3 * n_sm * n_pts_cta + n_pts_cta // 2 + 5       # >= 3 tiles per CTA, last tile ragged
+    assert (n + n_pts_cta - 1) // n_pts_cta >= 3 * n_sm and n % n_pts_cta != 0
+    idx = np.sort(syn.rng(11).choice(n, 40, replace=False))
     F = syn.fbar_batch(syn.SEED_BASE + 40, 2, n, 0.1, 0.3)
     q = np.zeros((n, h.nmax))
     s = np.zeros((n, h.nmax))
@@ -362,11 +385,14 @@ def test_tensor_core_kernel_many_tiles(name):
         g = run_gpu(h, F, q, s, S, U, 'fp64')
         q, s, S, U = g['q'], g['s'], g['S'], g['Uprev']
     q = q + syn.perturbation(syn.SEED_BASE + 42, q.shape, 1.0) * 1e-3 * np.abs(q).max(axis=1, keepdims=True)
+    # the sampled points carry states the oracle converged (inputs from the
+    # oracle only, so that the comparison does not rest on the GPU)
     Fm, qm, sm, Sm, Um = mid_newton_inputs(orom, len(idx), syn.SEED_BASE + 41)
     F[idx], q[idx], s[idx], S[idx], U[idx] = Fm, qm, sm, Sm, Um
     rv.rve_rom_select_kernel(h, 0, 'mixed', 0)
     ref = run_gpu(h, F, q, s, S, U, 'mixed')
-    rv.rve_rom_select_kernel(h, 0, 'mixed', nc - 1)
+    rv.rve_rom_select_kernel(h, 0, 'mixed', cand)
+    assert rv.rve_rom_kernel_info(h, 0, 'mixed')[0] == cname
     g = run_gpu(h, F, q, s, S, U, 'mixed')
     assert np.all(g['status'] == 0) and np.all(ref['status'] == 0)
     scale = np.abs(ref['Pbar']).max(axis=1)
@@ -376,6 +402,11 @@ def test_tensor_core_kernel_many_tiles(name):
     assert np.array_equal(g['q'], ref['q']) and np.array_equal(g['Uprev'], ref['Uprev'])
     compare({k: v[idx] for k, v in g.items()}, oracle_batch(oroms, F[idx], q[idx], s[idx], S[idx], U[idx]),
             h.nmax, TOL_MIXED)
+    # a second call on the same inputs: the same results (no state left
+    # behind in the workspace records or the per-CTA phase counters)
+    g2 = run_gpu(h, F, q, s, S, U, 'mixed')
+    for k in ('Pbar', 'dPdF', 's', 'S', 'q', 'rnorm', 'status'):
+        assert np.array_equal(g2[k], g[k]), k
 
 
 @pytest.mark.parametrize('name,n_keep', [('c1', 10), ('c2', 20), ('c2', 17)])

@@ -18,6 +18,14 @@ it.  Every data hazard the barriers guard is asserted:
 Two fold waits that are wrong pin the model's sensitivity: waiting for the
 last k-step's commit on a per-buffer barrier (two phases per chunk) lets the
 fold run early, and waiting for its two phases in turn blocks for good.
+
+Timeouts: every wait of the kernels gives up after a bounded time.  The model
+injects such timeouts at random blocked polls.  After the first one the CTA's
+error flag is set: no wait blocks any more, no MMA or bulk copy is issued,
+and the data hazards above are expected (the points are marked as timed out),
+but every role must still finish, and TMEM may be freed only once every MMA
+the tile warps issued has completed and every copy has landed (the drain at
+the end of the kernels).  Leaving the drain out is caught.
 The single-role kernel (csrc/rom_tc.cuh: 8 warps, a CTA barrier per chunk)
 is modelled too; its earlier per-buffer fold wait passes early whenever a
 warp is two k-steps behind, which random schedules reach.
@@ -53,8 +61,13 @@ class Hazard(AssertionError):
     pass
 
 
-def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
+def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeout_at=None, drain=True,
+                 latency=30, clock=False):
+    """timeout_at: the first wait still blocked at or after this model time
+    runs out.  Returns True when a timeout was injected; raises Hazard."""
     rng = random.Random(seed)
+    err = [False]                        # the CTA's timeout flag
+    inflight = {'mma': [0] * NW, 'copy': 0}
     bx = [Barrier(1), Barrier(1)]
     commit = [[Barrier(1), Barrier(1)] for _ in range(NW)]
     chunk = [Barrier(1) for _ in range(NW)]
@@ -70,18 +83,28 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
     wp_written, res_done, landed, readers, y_busy = {}, {}, set(), {}, {}
 
     def check(cond, what):
-        if not cond:
+        # data hazards are expected once a wait timed out (the points are
+        # marked, their outputs discarded)
+        if not cond and not err[0]:
             raise Hazard(what)
 
     def later(action, warp=None):
-        t = now[0] + rng.randint(1, 30)
+        t = now[0] + rng.randint(1, latency)
         if warp is not None:                 # one warp's MMAs complete in order
             t = max(t, last_mma.get(warp, 0) + 1)
             last_mma[warp] = t
         events.append((t, action))
 
     def wait(bar, parity):
-        while not bar.passed(parity):
+        while not bar.passed(parity) and not err[0]:
+            if timeout_at is not None and now[0] >= timeout_at:   # the bounded wait runs out
+                err[0] = True
+                return
+            yield
+
+    def drain_wait(cond):
+        # the end-of-kernel drain: bounded too, but the engines always finish
+        while not cond():
             yield
 
     def sync(i):
@@ -94,17 +117,25 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
             yield
 
     def stage(g):
+        if err[0]:                           # nothing is issued after a timeout
+            return
         b = g & 1
         check(readers.get(g - 2, 0) == 0, 'tables of chunk %d overwritten while read' % (g - 2))
         if g >= 2:
             check(all((w, g - 2) in mma_done for w in range(NW)), 'B image of chunk %d overwritten' % (g - 2))
 
         def land():
+            inflight['copy'] -= 1
             landed.add(g)
             for _ in range(NH):
                 staged[b].arrive()
+
+        def land_bx():
+            inflight['copy'] -= 1
+            bx[b].arrive()
+        inflight['copy'] += 2
         later(land)
-        later(bx[b].arrive)
+        later(land_bx)
 
     def helper(h):
         gc = gs = 0
@@ -149,6 +180,15 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
             gc += nch
             gs += nch * KSC
             yield from sync(0)
+        if drain and h == 0:
+            yield from drain_wait(lambda: inflight['copy'] == 0)
+        yield from sync(0)                   # the CTA barrier before TMEM is freed
+        if h == 0:
+            free_tmem()
+
+    def free_tmem():
+        if any(inflight['mma']) or inflight['copy']:
+            raise Hazard('TMEM freed or CTA ended with MMAs or copies in flight')
 
     def tile(w):
         gc = gs = 0
@@ -178,11 +218,15 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
                         if g >= 1:
                             yield from wait(fold, (g - 1) & 1)
                             check(len(folded.get((w, g - 1), ())) == NH, 'MMAs of chunk %d before the fold' % g)
+                    if err[0]:                   # no MMA is issued after a timeout
+                        continue
                     mma_issued.add((w, g))
                     y_busy[(w, yb)] = y_busy.get((w, yb), 0) + 1
                     last = ks == KSC - 1
+                    inflight['mma'][w] += 1
 
                     def complete(w=w, yb=yb, g=g, last=last):
+                        inflight['mma'][w] -= 1
                         y_busy[(w, yb)] -= 1
                         commit[w][yb].arrive()
                         if last:
@@ -194,6 +238,9 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
             gc += nch
             gs += nch * KSC
             yield from sync(0)
+        if drain:                            # commit + wait: all of this warp's MMAs completed
+            yield from drain_wait(lambda: inflight['mma'][w] == 0)
+        yield from sync(0)
 
     agents = [helper(h) for h in range(NH)] + [tile(w) for w in range(NW)]
     alive = list(range(len(agents)))
@@ -211,11 +258,41 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
             next(agents[i])
         except StopIteration:
             alive.remove(i)
+    return now[0] if clock else err[0]
 
 
 @pytest.mark.parametrize('seed', range(40))
 def test_protocol_is_hazard_free(seed):
-    run_schedule(seed, n_tiles=1 + seed % 3, nch=1 + (seed // 3) % 6)
+    assert not run_schedule(seed, n_tiles=1 + seed % 3, nch=1 + (seed // 3) % 6)
+
+
+@pytest.mark.parametrize('seed', range(30))
+def test_timeouts_end_the_kernel_after_a_drain(seed):
+    # random timeouts: every role finishes, and nothing is in flight when
+    # TMEM is freed
+    # (the timeout time is uniform over the run, or within the last MMA
+    # latency of its end, where MMAs of the last chunk are still in flight)
+    nt, nch = 1 + seed % 3, 1 + (seed // 3) % 6
+    latency = 30 if seed % 2 else 400
+    span = run_schedule(seed, nt, nch, latency=latency, clock=True)
+    r = random.Random(seed)
+    at = r.randrange(span) if seed % 3 else max(0, span - r.randrange(1, latency))
+    run_schedule(seed, nt, nch, latency=latency, timeout_at=at)
+
+
+def test_missing_drain_is_caught():
+    # timeouts during the last chunks, without the drain: some schedules free
+    # TMEM while MMAs still run
+    hits = 0
+    for seed in range(6):
+        span = run_schedule(seed, n_tiles=2, nch=4, latency=400, clock=True)
+        for back in range(100, 1600, 100):
+            try:
+                run_schedule(seed, n_tiles=2, nch=4, latency=400, drain=False, timeout_at=span - back)
+            except Hazard as e:
+                assert 'in flight' in str(e)
+                hits += 1
+    assert hits > 0
 
 
 @pytest.mark.parametrize('variant, what', [('buffer', 'before its MMAs completed'), ('two-phase', 'no progress')])
@@ -230,7 +307,8 @@ def test_wrong_fold_waits_are_caught(variant, what):
     assert hits > 0
 
 
-def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
+def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeout_at=None, drain=True,
+                    latency=30, clock=False):
     """Protocol of the single-role kernel (csrc/rom_tc.cuh): 8 warps, each
     issuing its own tile's MMAs per k-step and folding one lane quarter of
     every tile after the chunk, then a CTA barrier; returns nothing, raises
@@ -241,18 +319,22 @@ def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
     cta = NamedBarrier(NW)
     events, last_mma, now = [], {}, [0]
     mma_done, folds = set(), {}
+    err, inflight = [False], [0] * NW
 
     def check(cond, what):
-        if not cond:
+        if not cond and not err[0]:
             raise Hazard(what)
 
     def later(action, warp):
-        t = max(now[0] + rng.randint(1, 30), last_mma.get(warp, 0) + 1)
+        t = max(now[0] + rng.randint(1, latency), last_mma.get(warp, 0) + 1)
         last_mma[warp] = t
         events.append((t, action))
 
     def wait(bar, parity):
-        while not bar.passed(parity):
+        while not bar.passed(parity) and not err[0]:
+            if timeout_at is not None and now[0] >= timeout_at:
+                err[0] = True
+                return
             yield
 
     def sync():
@@ -274,9 +356,13 @@ def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
                     yield
                     check(all(folds.get((t, gchunk - 1), 0) == NW for t in range(NW)) or ch == 0 and gchunk == 0,
                           'MMAs before the fold of the previous chunk')
+                    if err[0]:                   # no MMA is issued after a timeout
+                        continue
                     last = ks == KSC - 1
+                    inflight[w] += 1
 
                     def complete(w=w, s=s, g=gchunk, last=last):
+                        inflight[w] -= 1
                         commit[w][s & 1].arrive()
                         if last:
                             mma_done.add((w, g))
@@ -295,6 +381,12 @@ def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
                     yield
                 yield from sync()
                 gchunk += 1
+        if drain:                                # commit + bounded wait
+            while inflight[w]:
+                yield
+        yield from sync()
+        if w == 0 and any(inflight):
+            raise Hazard('TMEM freed with MMAs in flight')
 
     agents = [warp(w) for w in range(NW)]
     alive = list(range(NW))
@@ -312,11 +404,33 @@ def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000):
             next(agents[i])
         except StopIteration:
             alive.remove(i)
+    return now[0] if clock else err[0]
 
 
 @pytest.mark.parametrize('seed', range(20))
 def test_single_role_protocol_is_hazard_free(seed):
     run_single_role(seed, n_tiles=1 + seed % 2, nch=1 + seed % 5)
+
+
+@pytest.mark.parametrize('seed', range(20))
+def test_single_role_timeouts_end_after_a_drain(seed):
+    nt, nch = 1 + seed % 2, 1 + seed % 5
+    span = run_single_role(seed, nt, nch, latency=400, clock=True)
+    for back in range(50, span, max(50, span // 10)):
+        run_single_role(seed, nt, nch, latency=400, timeout_at=span - back)
+
+
+def test_single_role_missing_drain_is_caught():
+    hits = 0
+    for seed in range(6):
+        span = run_single_role(seed, 1, 4, latency=400, clock=True)
+        for back in range(50, 1500, 50):
+            try:
+                run_single_role(seed, 1, 4, latency=400, drain=False, timeout_at=span - back)
+            except Hazard as e:
+                assert 'in flight' in str(e)
+                hits += 1
+    assert hits > 0
 
 
 def test_single_role_buffer_wait_is_caught():
