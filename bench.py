@@ -169,23 +169,119 @@ def aggregate(ms_local, n_local, world, dist=None, device='cpu'):
     return ms, world * n_local / (ms * 1e-3)
 
 
-def oracle_rate(rom_paths, types, F, q, s, S, U, budget_s, max_points=None):
-    """Evaluations/s of the float64 oracle (single thread) on a bounded sample."""
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(['lscpu'], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith('Model name:'):
+                return line.split(':', 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open('/proc/cpuinfo'):
+            if line.lower().startswith('model name'):
+                return line.split(':', 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+_WORKER = {}
+
+
+def _oracle_worker_init(rom_paths):
     from oracle import reduced
-    roms = [reduced.Rom.load(p) for p in rom_paths]
-    n = len(F)
-    cnt = 0
+    _WORKER['roms'] = [reduced.Rom.load(p) for p in rom_paths]
+
+
+def _oracle_worker_run(job):
+    """Evaluate the points of one chunk with the float64 oracle (fresh state
+    at each point's Fbar): once through the chunk (budget None), or cycling
+    until `budget` seconds have passed.  Returns (evaluations, seconds)."""
+    from oracle import polar, reduced, rve
+    types, F, budget = job
+    roms = _WORKER['roms']
+    states = []
+    for a in range(len(F)):
+        st = reduced.zero_state(roms[types[a]])
+        st['Uprev'] = rve.to_voigt(polar.polar(F[a])[1])
+        states.append(st)
+    cnt, a = 0, 0
     t0 = time.perf_counter()
-    a = 0
     while True:
-        r = roms[types[a]]
-        k = r.n
-        reduced.eval_point(r, F[a], q[a][:k], s[a][:k], S[a][:k], U[a])
+        reduced.eval_point(roms[types[a]], F[a], **states[a])
         cnt += 1
-        a = (a + 1) % n
+        a = (a + 1) % len(F)
         el = time.perf_counter() - t0
-        if el >= budget_s or (max_points and cnt >= max_points):
-            return cnt / el, cnt, el
+        if (budget is None and cnt == len(F)) or (budget is not None and el >= budget):
+            return cnt, el
+
+
+class OraclePool:
+    """The float64 oracle as it stands, one process per host core (spawned
+    processes, one NumPy thread each)."""
+
+    def __init__(self, rom_paths, cores):
+        import multiprocessing
+        self.cores = cores
+        self.pool = multiprocessing.get_context('spawn').Pool(cores, initializer=_oracle_worker_init,
+                                                              initargs=(rom_paths,))
+
+    def chunks(self, types, F, budget):
+        k = self.cores
+        return [(types[i::k], F[i::k], budget) for i in range(k) if len(F[i::k])]
+
+    def run(self, types, F, budget=None):
+        return self.pool.map(_oracle_worker_run, self.chunks(types, F, budget), chunksize=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def native_cpu_rate(rom_list, types_np, F, sel_all, nthreads, target_s=1.0, runs=5):
+    """Median of `runs` timings (evaluations/s) of the plain C++ float64
+    baseline on `nthreads` threads over a sample of the workload's points
+    sized to take about target_s seconds per run (fresh states).  Returns
+    (rate, threads used, points per run)."""
+    import cpu_baseline
+
+    def one(sel):
+        t0 = time.perf_counter()
+        used = 1
+        for t, rom in enumerate(rom_list):
+            idx = sel[types_np[sel] == t]
+            if len(idx) == 0:
+                continue
+            m, g, nm = rom['B'].shape
+            d = int(round(np.sqrt(g)))
+            ns = 3 if d == 2 else 6
+            q = np.zeros((len(idx), nm))
+            s_ = np.zeros((len(idx), nm))
+            S_ = np.zeros((len(idx), nm, ns))
+            U_ = np.zeros((len(idx), ns))
+            U_[:, :d] = 1.0
+            _, used = cpu_baseline.eval_batch(rom, F[idx], q, s_, S_, U_, nthreads=nthreads)
+        return time.perf_counter() - t0, used
+    probe = sel_all[:max(8, 2 * nthreads)]
+    dt, _ = one(probe)
+    per_pt = dt / len(probe)
+    npts = int(min(len(sel_all), max(len(probe), target_s / max(per_pt, 1e-9))))
+    sel = sel_all[:npts]
+    times, used = [], 1
+    for _ in range(runs):
+        dt, used = one(sel)
+        times.append(dt)
+    return npts / statistics.median(times), used, npts
 
 
 def oracle_accuracy(rom_paths, types_np, F_or, sel, seed):
@@ -450,56 +546,84 @@ def main():
         dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (the batched RVE evaluation)
+    # roofline of the dominant kernel (the batched RVE evaluation call:
+    # the evaluation kernel and, in the tensor-core form, its condensation
+    # kernel), one fraction per execution unit, against peaks measured live
+    # on this device by the library's probes
     kinfo = [rv.rve_rom_kernel_info(h, t, args.precision) for t in range(len(roms))]
     n_per_type = np.bincount(types_np, minlength=len(roms))
     w64 = sum(c * work_per_eval(r)[0] for c, r in zip(n_per_type, roms))
     w32 = sum(c * work_per_eval(r)[1] for c, r in zip(n_per_type, roms))
-    # algorithmic FLOPs (method-required work per evaluation x evaluations per launch)
-    # against the pipe that executes them: the FP64 form runs everything on
-    # the FP64 pipe; the mixed form runs the FP64-accurate part as double-float
-    # and the tangent contraction in float32, both on the FP32 pipe
-    achieved = (w64 + w32) / (ms_kern * 1e-3) / 1e12
-    if args.precision == 'fp64':
-        peak, unitname = 1.25, 'FP64 pipe'
-        src = 'nominal: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (measured 1.01 TFLOP/s in a DFMA probe)'
-    else:
-        peak, unitname = 80.5, 'FP32 pipe (double-float emulation of the FP64-accurate part)'
-        src = 'nominal: 152 SMs x 128 FFMA/clk x 2 FLOP x 2.07 GHz (measured 74.1 TFLOP/s in an FFMA probe)'
-    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
-                "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get((args.workload, args.precision)),
-                "kernel": "; ".join(nm for nm, _ in kinfo) + (" (selected)" if args.candidate >= 0 else " (autotuned)"),
-                "binding": unitname,
-                "peak_source": src, "kernel_ms": ms_kern,
-                "algorithmic_flop_per_eval": {"fp64_accurate": w64 / n, "fp32": w32 / n}}
-    # the other two units, for reference: the tensor pipe (the contraction's
-    # algorithmic FLOPs against the TF32 peak: measured bf16 x the nominal
-    # TF32 / BF16 ratio 1.1 / 2.25) and HBM (the profiled DRAM bytes per launch)
+    probe = {u: rv.rverom_peak_probe(u) for u in ('fp32', 'fp64', 'tf32', 'bf16')}
     try:
-        peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
-        tf32_peak, hbm_peak, psrc = peaks['bf16_tflops'] * 1.1 / 2.25, peaks['hbm_gbs'], 'measured'
+        hbm_peak, hsrc = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))['hbm_gbs'], 'measured copy'
     except (OSError, KeyError, ValueError):
-        tf32_peak, hbm_peak, psrc = 1900.0 * 1.1 / 2.25, 6800.0, 'fallback'
-    tensor_ach = w32 / (ms_kern * 1e-3) / 1e12
-    roofline["other_units"] = {
-        "tensor": {"achieved": tensor_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tensor_ach / tf32_peak,
-                   "peak_source": psrc + " bf16 x 1.1/2.25 (TF32)",
-                   "note": "algorithmic contraction FLOPs; the tensor-core form issues three TF32 passes"},
-        "hbm": None if roofline["traffic"] is None else {
-            "achieved": roofline["traffic"] / (ms_kern * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-            "frac": roofline["traffic"] / (ms_kern * 1e-3) / 1e9 / hbm_peak, "peak_source": psrc}}
-
+        hbm_peak, hsrc = 6800.0, 'fallback'
+    t_s = ms_kern * 1e-3
+    traffic = PROFILED_TRAFFIC.get((args.workload, args.precision))
+    kname = "; ".join(nm for nm, _ in kinfo) + (" (selected)" if args.candidate >= 0 else " (autotuned)")
+    units = {}
+    # a5: the reduced-tangent contraction's algorithmic FLOPs (symmetric half
+    # plus the Y products) against the tcgen05 TF32 rate
+    units["tensor"] = {"achieved": w32 / t_s / 1e12, "peak": probe['tf32'], "unit": "TFLOP/s",
+                       "frac": w32 / t_s / 1e12 / probe['tf32'],
+                       "peak_source": "measured: tcgen05.mma kind::tf32 probe (rverom_peak_probe)",
+                       "work": "a5 contraction, %.0f FLOP per evaluation" % (w32 / n)}
+    if args.precision == 'mixed':
+        # a2-a4: FP64-accurate kinematics, law and residual as double-float
+        # on the FP32 pipe; one double-float multiply-add (2 FLOP) costs 12
+        # FP32-pipe instructions, so the pipe's FP64-accurate peak is its
+        # FMA rate (2 FLOP per instruction) x 2 / 24
+        pk = probe['fp32'] / 12.0
+        units["alu"] = {"achieved": w64 / t_s / 1e12, "peak": pk, "unit": "TFLOP/s", "frac": w64 / t_s / 1e12 / pk,
+                        "peak_source": "measured FP32 FMA rate %.1f TFLOP/s / 12 (double-float multiply-add: "
+                                       "12 FP32 instructions for 2 FLOP)" % probe['fp32'],
+                        "work": "a2-a4 FP64-accurate, %.0f FLOP per evaluation" % (w64 / n)}
+    else:
+        units["alu"] = {"achieved": (w64 + w32) / t_s / 1e12, "peak": probe['fp64'], "unit": "TFLOP/s",
+                        "frac": (w64 + w32) / t_s / 1e12 / probe['fp64'],
+                        "peak_source": "measured FP64 FMA rate (rverom_peak_probe)",
+                        "work": "a2-a5 in float64, %.0f FLOP per evaluation" % ((w64 + w32) / n)}
+    if traffic is not None:
+        units["hbm"] = {"achieved": traffic / t_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": traffic / t_s / 1e9 / hbm_peak, "peak_source": hsrc,
+                        "work": "DRAM bytes per launch from an ncu capture of this workload"}
+    binding = max(units, key=lambda k: units[k]["frac"])
+    head = "tensor" if args.precision == 'mixed' else "alu"
+    roofline = dict(units[head])
+    roofline.update({"bound": head, "traffic": traffic, "kernel": kname, "kernel_ms": ms_kern,
+                     "binding_unit": binding, "units": units, "probe_tflops": probe,
+                     "note": "frac is the %s fraction; the unit with the largest fraction (binding_unit) "
+                             "limits the kernel" % head})
     cpu = None
+    cpu_native = None
     if world == 1 and not args.no_cpu_baseline:
-        Fh = Fbar.cpu().numpy().reshape(n, d, d)
-        sel = np.arange(0, n, max(1, n // 512))[:512]
-        restore()
-        st = [x.cpu().numpy() for x in (q, s, S, U)]
-        rate, cnt, el = oracle_rate(rom_paths, types_np[sel], Fh[sel], st[0][sel], st[1][sel], st[2][sel],
-                                    st[3][sel], budget_s=12.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d evaluations (cycling over %d of the %d points) in %.1f s, float64 NumPy oracle, one thread"
-                         % (cnt, len(sel), n, el)}
+        # the oracle as it stands, one process per host core, on a bounded
+        # sample of the workload's points (fresh states at the oracle's own
+        # Fbar of the same displacement field), for about 10 s
+        from oracle import macro as omacro
+        F_or = omacro.MacroMesh(X, conn).gradient(u_host)
+        cores = host_cores()
+        sel = np.sort(syn.rng(syn.SEED_BASE + 810).choice(n, min(n, 64 * cores), replace=False))
+        pool = OraclePool(rom_paths, cores)
+        pool.run(types_np[sel][:cores], F_or[sel][:cores])          # workers loaded and warm
+        res = pool.run(types_np[sel], F_or[sel], budget=10.0)
+        pool.close()
+        cnt = sum(c for c, _ in res)
+        el = max(e for _, e in res)
+        cpu = {"value": cnt / el, "unit": UNIT, "cores": len(res), "kind": "oracle",
+               "sample": "%d evaluations in %.1f s on %d processes (one NumPy thread each), each cycling over "
+                         "its share of %d sampled points of the %d, fresh micro states; float64 NumPy oracle; "
+                         "host %s, %d cores" % (cnt, el, len(res), len(sel), n, cpu_model(), cores)}
+        # the plain C++ float64 a1-a7 loop (OpenMP over points) on all host
+        # cores and on one, median of 5 runs
+        sel_n = syn.rng(syn.SEED_BASE + 811).permutation(n)
+        r_all, th_all, np_all = native_cpu_rate(roms, types_np, F_or.reshape(n, -1), sel_n, cores)
+        r_one, th_one, np_one = native_cpu_rate(roms, types_np, F_or.reshape(n, -1), sel_n, 1)
+        cpu_native = {"kind": "plain C++ float64 a1-a7, OpenMP over points (cpu_baseline/)", "unit": UNIT,
+                      "all_cores": {"value": r_all, "threads": th_all, "points_per_run": np_all},
+                      "one_core": {"value": r_one, "threads": th_one, "points_per_run": np_one},
+                      "statistic": "median of 5 runs", "nproc": cores, "cpu_model": cpu_model()}
 
     # our kernels per step: gradient, (bucketing: 3 with several types),
     # the evaluation kernels of every type, assembly, norms
@@ -517,6 +641,7 @@ def main():
                    "failed_points": bad},
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "cpu_native": cpu_native,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(u_pin.numel() * 8),
                 "d2h_bytes_per_step": int((R_pin.numel() + K_pin.numel() + 3) * 8)},
@@ -537,48 +662,36 @@ def main():
 
 
 def run_reference(args, wl, rom_paths, X, conn, u_host):
-    """The oracle as it stands on the host cores, same metric and workload:
-    each step is a bounded sample of the workload's macro points."""
-    from oracle import macro as omacro, reduced
-    d = wl['d']
+    """The oracle as it stands on the host cores (one process per core),
+    same metric and workload: each step evaluates a bounded sample of the
+    workload's macro points (fresh micro states)."""
+    from oracle import macro as omacro
     mesh = omacro.MacroMesh(X, conn)
     Fh = mesh.gradient(u_host)
     n = mesh.n_ip
     types = np.zeros(n, dtype=np.int64)
     if len(rom_paths) > 1:
         types = syn.type_labels(syn.SEED_BASE + 600, n, len(rom_paths)).astype(np.int64)
-    roms = [reduced.Rom.load(p) for p in rom_paths]
-    per_step = 1024
+    cores = host_cores()
+    per_step = min(n, max(4096, 256 * cores))
     sel = np.arange(0, n, max(1, n // per_step))[:per_step]
-    states = []
-    for a in sel:
-        r = roms[types[a]]
-        st = reduced.zero_state(r)
-        from oracle import polar, rve
-        st['Uprev'] = rve.to_voigt(polar.polar(Fh[a])[1])
-        states.append(st)
-
-    def one_step():
-        for k, a in enumerate(sel):
-            r = roms[types[a]]
-            o = reduced.eval_point(r, Fh[a], **states[k])
-        return o
-
+    pool = OraclePool(rom_paths, cores)
     for _ in range(args.warmup):
-        one_step()
+        pool.run(types[sel], Fh[sel])
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        one_step()
+        pool.run(types[sel], Fh[sel])
     el = time.perf_counter() - t0
+    pool.close()
     rate = len(sel) * args.steps / el
+    sample = ("%d of the %d macro points per step (fresh micro states), float64 NumPy oracle on %d processes "
+              "(one NumPy thread each); host %s" % (len(sel), n, cores, cpu_model()))
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": args.workload + ': ' + wl['desc'], "sample_points_per_step": len(sel)},
-           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "%d of the %d macro points per step, float64 NumPy oracle, one thread"
-                                      % (len(sel), n)},
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -232,6 +232,27 @@ int macro_assemble(rverom_mesh_t m, const double *Pbar, const double *dPdF, doub
 int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_mask,
                          int64_t n_points, const double *rnorm, double *out, void *stream);
 
+/* ---- diagnostics (no counterpart in the paper) -------------------------- */
+
+/* The double-float natural logarithm that the mixed form's micro law uses
+ * for ln J (range reduction to [1/sqrt2, sqrt2) and an atanh series, about
+ * 1e-14 relative), evaluated at n device points x [n] (each rounded to a
+ * double-float first) into device out [n] (float64).  For testing that
+ * routine against float64 log; x must be finite and positive. */
+int rverom_df_log(int64_t n, const double *x, double *out, void *stream);
+
+/* Measured throughput, in TFLOP/s, of one execution unit of the current
+ * device, the denominators of the roofline fractions of the hot path:
+ *   unit 0  FP32 FMA pipe (independent FMA chains, 2 FLOP per FMA)
+ *   unit 1  FP64 FMA pipe (the same with doubles)
+ *   unit 2  tcgen05.mma kind::tf32, M = 128, N = 256, K = 8
+ *   unit 3  tcgen05.mma kind::f16 with BF16 operands, M = 128, N = 256, K = 16
+ * One CTA per SM (MMAs) or 8 CTAs of 256 threads per SM (FMAs); the best
+ * of three timed runs (CUDA events) after one warm-up.  Synchronous on
+ * `stream`; allocates and frees 4 KB of device memory.  RVEROM_ERR_CUDA if
+ * a launch fails or an MMA completion wait runs out. */
+int rverom_peak_probe(int32_t unit, double *tflops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -265,3 +265,23 @@ def macro_residual_norms(m, R, free_mask, rnorm, out, stream=None):
         m.ptr, _ptr(R, torch.float64, (m.n_dof,), 'R'), _ptr(free_mask, torch.uint8, (m.n_dof,), 'free_mask'),
         n, _ptr(rnorm, torch.float64, (n,), 'rnorm'), _ptr(out, torch.float64, (3,), 'out'),
         _stream(stream)), 'macro_residual_norms')
+
+
+def rverom_df_log(x, out, stream=None):
+    """The library's double-float logarithm at the points of x (float64, CUDA)."""
+    n = x.shape[0]
+    _native.check(_native.lib().rverom_df_log(n, _ptr(x, torch.float64, (n,), 'x'),
+                                              _ptr(out, torch.float64, (n,), 'out'), _stream(stream)),
+                  'rverom_df_log')
+
+
+PEAK_UNITS = {'fp32': 0, 'fp64': 1, 'tf32': 2, 'bf16': 3}
+
+
+def rverom_peak_probe(unit, stream=None):
+    """Measured TFLOP/s of one execution unit ('fp32', 'fp64', 'tf32' or
+    'bf16') of the current device."""
+    v = ctypes.c_double()
+    _native.check(_native.lib().rverom_peak_probe(PEAK_UNITS[unit], ctypes.byref(v), _stream(stream)),
+                  'rverom_peak_probe')
+    return v.value

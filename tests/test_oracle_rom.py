@@ -65,6 +65,32 @@ def test_rom_error_falls_with_modes():
     assert np.abs(Phi.T @ Phi - np.eye(12)).max() < 1e-10
 
 
+def test_pod_split_spans_the_elastic_range_and_the_remaining_snapshots():
+    # Eqs. SVD_displacement / snapshots_displacement: Phi_el spans the linear
+    # responses to the unit macro strains; Phi_inel is orthogonal to it and
+    # is the best rank-k basis of the snapshots with their Phi_el part
+    # removed: the projection error equals the sum of the discarded
+    # eigenvalues of the Gram matrix of those snapshots (computed here by a
+    # symmetric eigen-solver, not an SVD)
+    m = model(2, 10)
+    X = rom.snapshots(m, _paths(2, 6, 4, 0.12, seed=8))
+    Wel = m.linear_responses()
+    nel = 3
+    for k in (2, 5):
+        Phi = rom.pod_basis(m, X, nel + k)
+        Pel, Pin = Phi[:, :nel], Phi[:, nel:]
+        assert np.linalg.norm(Wel - Pel @ (Pel.T @ Wel)) < 1e-12 * np.linalg.norm(Wel)
+        assert np.abs(Pel.T @ Pin).max() < 1e-10
+        Xm = X - Wel @ np.linalg.solve(Wel.T @ Wel, Wel.T @ X)       # remove the elastic part
+        ev = np.sort(np.linalg.eigvalsh(Xm.T @ Xm))[::-1]
+        err2 = np.linalg.norm(Xm - Pin @ (Pin.T @ Xm)) ** 2
+        assert abs(err2 - ev[k:].sum()) <= 1e-8 * ev.sum()
+    # a basis that skipped the removal of the elastic part would not be
+    # orthogonal to it
+    Uraw = np.linalg.svd(X, full_matrices=False)[0][:, :2]
+    assert np.abs(Pel.T @ Uraw).max() > 1e-3
+
+
 @pytest.fixture(scope='module')
 def small_ecm():
     m = model(2, 8)
@@ -104,21 +130,71 @@ def test_ecm_exact_beyond_rank():
             assert np.abs(w @ f[z] - m.ip_weight @ f).max() < 1e-10
 
 
-def test_ecm_greedy_box1_on_tiny_system():
-    # brute-force check of the greedy's first pick and of the exact solve
-    rng = np.random.default_rng(4)
-    lam = np.linalg.qr(rng.standard_normal((9, 2)))[0]
-    J = np.vstack([lam.T, np.ones((1, 9))])
-    b = np.array([0.0, 0.0, 1.0])
-    score0 = (J.T @ b) / np.linalg.norm(J, axis=0)
-    z1, w1 = rom.ecm_greedy(J, b, 1)
-    assert z1[0] == int(np.argmax(score0))
-    # one point: the least-squares weight is the projection of b on j_k
-    jk = J[:, z1[0]]
-    assert abs(w1[0] - (jk @ b) / (jk @ jk)) < 1e-14
-    z, w = rom.ecm_greedy(J, b, 3)
-    if np.all(w > 0) and len(z) == 3:
-        assert np.abs(J[:, z] @ w - b).max() < 1e-13
+def _brute_force_nnls(A, b):
+    """min ||A w - b|| over w >= 0 by enumerating the supports: on each
+    support the unconstrained least-squares solution (normal equations),
+    kept if non-negative; the best feasible one wins."""
+    import itertools
+    n = A.shape[1]
+    best, best_w = np.inf, np.zeros(n)
+    for k in range(n + 1):
+        for sup in itertools.combinations(range(n), k):
+            w = np.zeros(n)
+            if k:
+                As = A[:, sup]
+                ws = np.linalg.solve(As.T @ As, As.T @ b)
+                if np.any(ws < -1e-13):
+                    continue
+                w[list(sup)] = ws
+            res = np.linalg.norm(A @ w - b)
+            if res < best - 1e-14:
+                best, best_w = res, w
+    return best_w
+
+
+def test_ecm_greedy_box1_on_tiny_system(monkeypatch):
+    # Box 1 on small random systems J = [lambda 1]^T, b = [0 V0]^T:
+    #  - the first pick is the column most aligned with b (brute force);
+    #  - one point: the least-squares weight is the projection of b on j_k;
+    #  - every non-negative solve of the loop (the NNLS of step 5) equals a
+    #    brute-force enumeration of supports, and zero weights are dropped;
+    #  - the result has positive weights that are the least-squares solution
+    #    on their support (J_z^T (b - J_z w) = 0);
+    #  - when the target count is reached with m~ = rows, J_z w = b exactly.
+    import scipy.optimize as spo
+    calls = []
+    real_nnls = spo.nnls
+
+    def nnls(A, b):
+        w = real_nnls(A, b)[0]
+        calls.append((A.copy(), b.copy(), w.copy()))
+        return w, np.linalg.norm(A @ w - b)
+    monkeypatch.setattr(rom.spo, 'nnls', nnls)
+    reached = 0
+    for seed in range(60):
+        rng = np.random.default_rng(seed)
+        m, k = 9, 2
+        lam = np.linalg.qr(rng.standard_normal((m, k)))[0]
+        J = np.vstack([lam.T, np.ones((1, m))])
+        b = np.zeros(k + 1)
+        b[-1] = 1.0
+        if seed == 0:
+            score0 = (J.T @ b) / np.linalg.norm(J, axis=0)
+            z1, w1 = rom.ecm_greedy(J, b, 1)
+            assert z1[0] == int(np.argmax(score0))
+            jk = J[:, z1[0]]
+            assert abs(w1[0] - (jk @ b) / (jk @ jk)) < 1e-14
+        z, w = rom.ecm_greedy(J, b, k + 1)
+        assert np.all(w > 0) and len(set(z.tolist())) == len(z)
+        r = b - J[:, z] @ w
+        assert np.abs(J[:, z].T @ r).max() < 1e-12
+        if len(z) == k + 1:
+            reached += 1
+            assert np.abs(r).max() < 1e-13
+    assert reached > 10                    # the exact-solve branch is exercised
+    assert len(calls) > 5                  # so is the non-negative solve
+    for A, bb, w in calls:
+        assert np.abs(w - _brute_force_nnls(A, bb)).max() < 1e-10
 
 
 def test_hyper_rom_converges_to_full_integration(small_ecm):
