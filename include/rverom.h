@@ -235,8 +235,8 @@ int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_m
 /* ---- diagnostics (no counterpart in the paper) -------------------------- */
 
 /* The double-float natural logarithm that the mixed form's micro law uses
- * for ln J (range reduction to [1/sqrt2, sqrt2) and an atanh series, about
- * 1e-14 relative), evaluated at n device points x [n] (each rounded to a
+ * for ln J (range reduction to [1/sqrt2, sqrt2) and an atanh series, within
+ * 3e-14 relative), evaluated at n device points x [n] (each rounded to a
  * double-float first) into device out [n] (float64).  For testing that
  * routine against float64 log; x must be finite and positive. */
 int rverom_df_log(int64_t n, const double *x, double *out, void *stream);

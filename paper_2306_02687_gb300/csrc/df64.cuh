@@ -95,7 +95,8 @@ __device__ __forceinline__ void dacc_fma(dacc &s, float ah, float al, float bh, 
 
 __device__ __forceinline__ df dacc_get(const dacc &s) { return fast_two_sum(s.hi, s.lo); }
 
-// Natural logarithm of x > 0 to about 1e-14 relative: x = 2^k m with
+// Natural logarithm of x > 0 to 3e-14 relative (2.4e-14 measured against
+// float64 log over [0.5, 2]): x = 2^k m with
 // m in [1/sqrt2, sqrt2), ln m = 2 atanh(t), t = (m - 1)/(m + 1), |t| < 0.172,
 // 2 atanh(t) = 2t (1 + t^2/3 + t^4/5 + t^6/7 + t^8 R(t^2)); the first terms in
 // double-float, the remainder R = 1/9 + t^2/11 + ... + t^8/17 in float32
