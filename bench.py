@@ -339,6 +339,9 @@ def main():
     ap.add_argument('--precision', default='mixed', choices=['mixed', 'fp64'])
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-adjoint', action='store_true', help='skip the timing of the implicit adjoint')
+    ap.add_argument('--no-newton', action='store_true',
+                    help='skip the timing of whole Newton iterations with the global macro solve')
     ap.add_argument('--no-oracle-check', action='store_true',
                     help='skip the per-output comparison with the float64 oracle on 256 sampled points')
     ap.add_argument('--candidate', type=int, default=-1,
@@ -542,6 +545,44 @@ def main():
         gms += g0.elapsed_time(g1)
     ms_graph, graph_value = aggregate(gms / args.steps, n, world, dist, dev)
 
+    # a whole monolithic Newton iteration on the device: the step above plus
+    # the global macro solve (macro_solve) and the update u += du, with the
+    # workload's boundary DOFs held at the synthetic field's values
+    # the implicit adjoint (rve_rom_adjoint) over every point at converged
+    # micro states: a cotangent on Pbar -> cotangents on Fbar and the moduli
+    adj = None
+    if not args.no_adjoint:
+        restore()
+        for _ in range(12):
+            rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision='fp64')
+        gP = torch.randn(n, d * d, dtype=torch.float64, device=dev,
+                         generator=torch.Generator(device=dev).manual_seed(syn.SEED_BASE + 710))
+        gF = torch.empty_like(gP)
+        gth = torch.zeros(len(roms), 2, 2, dtype=torch.float64, device=dev)
+        ast = torch.empty(n, dtype=torch.int32, device=dev)
+        for _ in range(args.warmup):
+            rv.rve_rom_adjoint(h, Fbar, q, gP, gF, gth, ast, type=types)
+        torch.cuda.synchronize()
+        ams = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            rv.rve_rom_adjoint(h, Fbar, q, gP, gF, gth, ast, type=types)
+            a1.record(stream)
+            a1.synchronize()
+            ams += a0.elapsed_time(a1)
+        ams /= args.steps
+        adj = {"value": n / (ams * 1e-3), "unit": "adjoint point evaluations/s", "ms_per_call": ams, "points": n,
+               "converged_rnorm_max": rnorm.max().item(), "failed_points": int((ast != 0).sum().item()),
+               "note": "rve_rom_adjoint (float64) at micro states converged by 12 float64 evaluations"}
+        restore()
+
+    newton = None
+    if not args.no_newton:
+        newton = newton_leg(rv, h, mesh, wl, u_host, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, types, R, Kv,
+                            restore, args, dev, stream, flush, world, dist)
+
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -648,6 +689,8 @@ def main():
         "gpu_launches": launches,
         "graph": {"value": graph_value, "ms_per_step": ms_graph,
                   "note": "gradient, evaluation, assembly and norms captured in one CUDA graph"},
+        "newton": newton,
+        "adjoint": adj,
         "clocks": clocks,
         "other_form": {"precision": other, "value": world * n / (ms_other * 1e-3), "ms_per_step": ms_other},
         "speedup_vs_fp64_form": (ms_other / ms_step) if args.precision == 'mixed' else 1.0,
@@ -659,6 +702,92 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def newton_leg(rv, h, mesh, wl, u_host, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, types, R, Kv, restore, args,
+               dev, stream, flush, world, dist):
+    """Time whole Newton iterations (gradient, evaluation, assembly, norms,
+    global solve and update) from the mid-Newton state, prescribed boundary
+    DOFs held at the synthetic field's values; also one iteration captured
+    in a CUDA graph."""
+    import torch
+    d = wl['d']
+    X, _ = build_mesh(wl['mesh'])
+    dofs, _ = meshes.boundary_dofs(wl['mesh'][0], X)
+    free_np = np.ones(mesh.n_dof, dtype=np.uint8)
+    free_np[dofs] = 0
+    free = torch.tensor(free_np, device=dev)
+    un = torch.tensor(u_host, device=dev)
+    norms = torch.empty(3, dtype=torch.float64, device=dev)
+    du = torch.empty(mesh.n_dof, dtype=torch.float64, device=dev)
+    K = max(args.steps, 3)
+    infos = torch.zeros(args.warmup + K, 3, dtype=torch.float64, device=dev)
+
+    def it(k):
+        rv.macro_gradient(mesh, un, Fbar)
+        rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=args.precision)
+        rv.macro_assemble(mesh, Pbar, dPdF, R, Kv)
+        rv.macro_residual_norms(mesh, R, free, rnorm, norms)
+        rv.macro_solve(mesh, Kv, R, free, u=un, du=du, info=infos[k], tol=1e-12)
+
+    restore()
+    for k in range(args.warmup):
+        it(k)
+    torch.cuda.synchronize()
+    tot, solve_ms = 0.0, 0.0
+    for k in range(K):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        rv.macro_gradient(mesh, un, Fbar)
+        rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=args.precision)
+        rv.macro_assemble(mesh, Pbar, dPdF, R, Kv)
+        rv.macro_residual_norms(mesh, R, free, rnorm, norms)
+        e[1].record(stream)
+        rv.macro_solve(mesh, Kv, R, free, u=un, du=du, info=infos[args.warmup + k], tol=1e-12)
+        e[2].record(stream)
+        e[2].synchronize()
+        tot += e[0].elapsed_time(e[2])
+        solve_ms += e[1].elapsed_time(e[2])
+    inf = infos.cpu().numpy()
+    nr = norms.cpu().numpy()
+    ms, value = aggregate(tot / K, mesh.n_ip, world, dist, dev)
+    out = {"value": value, "unit": UNIT, "ms_per_newton_iteration": ms, "solve_ms": solve_ms / K,
+           "iterations_timed": K, "cg_iterations": inf[args.warmup:, 0].astype(int).tolist(),
+           "cg_status": inf[args.warmup:, 2].astype(int).tolist(),
+           "residual_after": {"R_free_max": float(nr[0]), "R_prescribed_max": float(nr[1]),
+                              "micro_r_max": float(nr[2])},
+           "bc": "%s: %d prescribed DOFs held at the synthetic field's values" % (wl['mesh'][0], len(dofs)),
+           "solve": "macro_solve: block-Jacobi preconditioned CG, relative tolerance 1e-12"}
+    # the same Newton iteration captured in one CUDA graph
+    try:
+        restore()
+        un.copy_(torch.tensor(u_host, device=dev))
+        it(0)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph):
+                it(0)
+        restore()
+        un.copy_(torch.tensor(u_host, device=dev))
+        torch.cuda.synchronize()
+        gms = 0.0
+        for _ in range(K):
+            flush.zero_()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            graph.replay()
+            g1.record(stream)
+            g1.synchronize()
+            gms += g0.elapsed_time(g1)
+        out["graph_ms_per_newton_iteration"] = gms / K
+    except Exception as exc:  # capture of the cooperative launch refused
+        out["graph_ms_per_newton_iteration"] = None
+        out["graph_note"] = str(exc)[:200]
+    restore()
+    return out
 
 
 def run_reference(args, wl, rom_paths, X, conn, u_host):

@@ -232,6 +232,26 @@ int macro_assemble(rverom_mesh_t m, const double *Pbar, const double *dPdF, doub
 int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_mask,
                          int64_t n_points, const double *rnorm, double *out, void *stream);
 
+/* Global macro solve of a monolithic Newton iteration (Sec. 2: the Newton
+ * correction of the discrete macro equilibrium Eq. 6, linearized with the
+ * consistent tangent that macro_assemble assembles; the paper uses a direct
+ * solver, here conjugate gradients):
+ *   K du = -R   on the DOFs with free_mask != 0,   du = 0 on the others,
+ *   u += du     (when u is not NULL).
+ * Preconditioned by the inverse d x d diagonal block of every node (rows
+ * and columns of prescribed DOFs replaced by the identity); stops when
+ * ||r||_2 <= tol ||R_free||_2 or after max_iter iterations.  Runs as one
+ * cooperative kernel (one or two blocks per SM, in the mesh's workspace:
+ * no allocation, so the call can sit in a CUDA graph with the rest of the
+ * Newton iteration).  Calls on one mesh must not overlap.
+ * Device arrays: Kvals [nnz] (CSR of macro_mesh_csr), R [n_dof],
+ * free_mask [n_dof] uint8, u [n_dof] (in/out, may be NULL), du [n_dof] (out),
+ * info [3] (out): iterations, final relative residual, status (0 converged,
+ * 1 max_iter reached, 2 K not positive definite on a search direction,
+ * 5 an internal grid barrier ran out of time). */
+int macro_solve(rverom_mesh_t m, const double *Kvals, const double *R, const uint8_t *free_mask, double tol,
+                int32_t max_iter, double *u, double *du, double *info, void *stream);
+
 /* ---- diagnostics (no counterpart in the paper) -------------------------- */
 
 /* The double-float natural logarithm that the mixed form's micro law uses

@@ -10,11 +10,14 @@ implicit adjoint, as CUDA kernels behind the C ABI of include/rverom.h.
 Python entry points (thin marshalling over librverom.so, see api.py):
   rve_rom_create, rve_rom_set_moduli, rve_rom_autotune, rve_rom_select_kernel,
                   rve_rom_kernel_info, rve_rom_eval_batch, rve_rom_adjoint,
-  macro_mesh_create, macro_gradient, macro_assemble, macro_residual_norms
+  macro_mesh_create, macro_gradient, macro_assemble, macro_residual_norms,
+                  macro_solve (global Newton correction on the device)
+  rverom_df_log, rverom_peak_probe (diagnostics)
 """
 from .api import (FP64, MIXED, RomHandle, MeshHandle, load_rom_file, rve_rom_create,  # noqa: F401
                   rve_rom_set_moduli, rve_rom_autotune, rve_rom_select_kernel,
                   rve_rom_kernel_info, rve_rom_eval_batch, rve_rom_adjoint, rve_rom_adjoint_static,
                   macro_mesh_create,
-                  macro_gradient, macro_assemble, macro_residual_norms, rverom_df_log, rverom_peak_probe)
+                  macro_gradient, macro_assemble, macro_residual_norms, macro_solve, rverom_df_log,
+                  rverom_peak_probe)
 from .autograd import RveStress, rve_stress  # noqa: F401

@@ -42,6 +42,7 @@ SIGNATURES = {
     'macro_gradient': (c_int, [c_vp, c_vp, c_vp, c_vp]),
     'macro_assemble': (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'macro_residual_norms': (c_int, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    'macro_solve': (c_int, [c_vp, c_vp, c_vp, c_vp, c_dbl, c_int, c_vp, c_vp, c_vp, c_vp]),
     'rverom_df_log': (c_int, [c_i64, c_vp, c_vp, c_vp]),
     'rverom_peak_probe': (c_int, [c_int, P(c_dbl), c_vp]),
 }

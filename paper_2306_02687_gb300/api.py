@@ -267,6 +267,25 @@ def macro_residual_norms(m, R, free_mask, rnorm, out, stream=None):
         _stream(stream)), 'macro_residual_norms')
 
 
+def macro_solve(m, Kvals, R, free_mask, u=None, du=None, info=None, tol=1e-12, max_iter=20000, stream=None):
+    """Newton correction of the macro problem on the device: K du = -R on the
+    free DOFs (du = 0 on the prescribed ones), u += du when u is given.
+    Returns (du, info) with info = [iterations, relative residual, status]
+    (device tensors; nothing is synchronized)."""
+    n = m.n_dof
+    if du is None:
+        du = torch.empty(n, dtype=torch.float64, device=R.device)
+    if info is None:
+        info = torch.empty(3, dtype=torch.float64, device=R.device)
+    _native.check(_native.lib().macro_solve(
+        m.ptr, _ptr(Kvals, torch.float64, (m.nnz,), 'Kvals'), _ptr(R, torch.float64, (n,), 'R'),
+        _ptr(free_mask, torch.uint8, (n,), 'free_mask'), float(tol), int(max_iter),
+        _ptr(u, torch.float64, (m.n_nodes, m.dim), 'u') if u is not None else None,
+        _ptr(du, torch.float64, (n,), 'du'), _ptr(info, torch.float64, (3,), 'info'), _stream(stream)),
+        'macro_solve')
+    return du, info
+
+
 def rverom_df_log(x, out, stream=None):
     """The library's double-float logarithm at the points of x (float64, CUDA)."""
     n = x.shape[0]

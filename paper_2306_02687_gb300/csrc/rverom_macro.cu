@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/rverom.h"
+#include "tc.cuh"
 
 struct rverom_mesh_s {
     int dim = 2, nen = 4, ngp = 4;
@@ -20,6 +21,15 @@ struct rverom_mesh_s {
     int32_t *kmap = nullptr;     // device [n_elem][(nen d)^2] CSR index of K_e entries
     std::vector<int64_t> row_ptr;
     std::vector<int32_t> col;
+    // global solve (macro_solve): device CSR pattern, CSR index of each
+    // row's diagonal-block start, and the solver's workspace
+    int32_t *rowp = nullptr;     // device [n_dof + 1]
+    int32_t *colv = nullptr;     // device [nnz]
+    int32_t *dpos = nullptr;     // device [n_dof]: index of entry (node d + i, node d) in row node d + i
+    double *work = nullptr;      // device: r, z, p, q, x [n_dof] each; block inverses [n_nodes][d][d]
+    double *part = nullptr;      // device [3][solve_blocks] per-block partial sums
+    unsigned *sync = nullptr;    // device [4]: grid-barrier count and generation, error flag
+    int solve_blocks = 0;
 };
 
 namespace {
@@ -159,6 +169,8 @@ __global__ void k_norms(int64_t n_dof, const double *R, const uint8_t *free_mask
     }
 }
 
+bool solve_setup(rverom_mesh_s *m, const std::vector<int32_t> &rowp32, const std::vector<int32_t> &dpos);
+
 int grid_for(int64_t work, int n_sm) {
     int64_t g = (work + 255) / 256;
     if (g > 8LL * n_sm) g = 8LL * n_sm;
@@ -261,6 +273,17 @@ extern "C" int macro_mesh_create(int32_t dim, int64_t n_nodes, int64_t n_elem, c
                             (int32_t)(m->row_ptr[node * d + i] + pos * d + k);
                 }
             }
+    if (m->nnz > INT32_MAX) {
+        delete m;
+        return RVEROM_ERR_ARG;
+    }
+    std::vector<int32_t> rowp32((size_t)m->n_dof + 1), dpos((size_t)m->n_dof);
+    for (size_t r = 0; r <= (size_t)m->n_dof; ++r) rowp32[r] = (int32_t)m->row_ptr[r];
+    for (int64_t node = 0; node < n_nodes; ++node) {
+        const auto &nb = adj[node];
+        const int64_t pos = std::lower_bound(nb.begin(), nb.end(), (int32_t)node) - nb.begin();
+        for (int i = 0; i < d; ++i) dpos[node * d + i] = (int32_t)(m->row_ptr[node * d + i] + pos * d);
+    }
     std::vector<int32_t> conn32((size_t)n_elem * nen);
     for (size_t x = 0; x < conn32.size(); ++x) conn32[x] = (int32_t)conn[x];
     bool ok = cudaMalloc(&m->conn, conn32.size() * 4) == cudaSuccess &&
@@ -270,6 +293,7 @@ extern "C" int macro_mesh_create(int32_t dim, int64_t n_nodes, int64_t n_elem, c
               cudaMemcpy(m->dN, dN.data(), dN.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(m->wJ0, wJ0.data(), wJ0.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(m->kmap, kmap.data(), kmap.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && solve_setup(m, rowp32, dpos);
     if (!ok) {
         macro_mesh_destroy(m);
         return RVEROM_ERR_CUDA;
@@ -285,6 +309,12 @@ extern "C" int macro_mesh_destroy(rverom_mesh_t m) {
     cudaFree(m->dN);
     cudaFree(m->wJ0);
     cudaFree(m->kmap);
+    cudaFree(m->rowp);
+    cudaFree(m->colv);
+    cudaFree(m->dpos);
+    cudaFree(m->work);
+    cudaFree(m->part);
+    cudaFree(m->sync);
     delete m;
     return RVEROM_OK;
 }
@@ -336,4 +366,323 @@ extern "C" int macro_residual_norms(rverom_mesh_t m, const double *R, const uint
     const int64_t work = m->n_dof > n_points ? m->n_dof : n_points;
     k_norms<<<grid_for(work, m->n_sm), 256, 0, st>>>(m->n_dof, R, free_mask, n_points, rnorm, out);
     return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Global macro solve: K du = -R on the free DOFs (du = 0 on the prescribed
+// ones), the Newton correction of the monolithic scheme (Sec. 2, Eq. 6 and
+// its linearization; the paper solves it with a direct solver).  Conjugate
+// gradients preconditioned by the inverse nodal d x d diagonal blocks of K,
+// in one persistent cooperative kernel: every block owns a slice of the
+// nodes and rows, and three grid barriers per iteration separate the sparse
+// product, the update and the next search direction.  Dot products are
+// reduced per block and summed by every block in the same order, so that
+// all blocks take the same convergence decision.
+namespace {
+
+constexpr int SOLVE_THREADS = 256;
+
+struct SolveArgs {
+    int64_t n_nodes, n_dof;
+    const int32_t *rowp, *col, *dpos;
+    const double *K, *R;
+    const uint8_t *free_mask;
+    double *u, *du, *info;
+    double tol;
+    int max_iter;
+    double *r, *z, *p, *q, *x, *minv, *part;
+    unsigned *sync;
+};
+
+// grid barrier with a bounded wait: false (and the error flag set) once any
+// block's wait has run out
+__device__ bool grid_barrier(unsigned *sync, unsigned nblk) {
+    __shared__ unsigned s_ok;  // one reading per block, so that all its threads agree
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = sync + 1;
+        volatile unsigned *verr = sync + 2;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(sync, 1u) == nblk - 1) {
+            atomicExch(sync, 0u);
+            __threadfence();
+            atomicAdd(sync + 1, 1u);
+        } else {
+            const uint64_t t0 = rverom::tc::globaltimer_ns();
+            while (*vgen == g && *verr == 0) {
+                if (rverom::tc::globaltimer_ns() - t0 > rverom::tc::WAIT_LIMIT_NS) {
+                    atomicExch(sync + 2, 1u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = *verr == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// sum of this block's values v over its threads (every thread gets the sum)
+__device__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < SOLVE_THREADS / 32; ++k) t += sh[k];
+    return t;
+}
+
+// sum of the per-block partials (written by other blocks: read past L1),
+// the same order in every block
+__device__ double grid_sum(const double *part, unsigned nblk, double *sh) {
+    double v = 0.0;
+    if (threadIdx.x < 32)
+        for (unsigned b = threadIdx.x; b < nblk; b += 32) v += __ldcg(part + b);
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh[8] = v;
+    __syncthreads();
+    return sh[8];
+}
+
+template <int D>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg(SolveArgs a) {
+    __shared__ double sh[16];
+    const unsigned nblk = gridDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)nblk * blockDim.x;
+    double *ppq = a.part, *prz = a.part + nblk, *prr = a.part + 2 * nblk;
+    // preconditioner: inverse of each node's diagonal block with the rows and
+    // columns of prescribed DOFs replaced by the identity; b = -R on the free
+    // DOFs; x = 0, r = b, z = M r, p = z
+    double bb = 0.0, rz0 = 0.0;
+    for (int64_t nd = tid; nd < a.n_nodes; nd += nth) {
+        double Bk[D * D], Bi[D * D];
+        bool fr[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) fr[i] = a.free_mask[nd * D + i] != 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                Bk[i * D + k] = (fr[i] && fr[k]) ? a.K[a.dpos[nd * D + i] + k] : (i == k ? 1.0 : 0.0);
+        double det;
+        if (D == 2) {
+            det = Bk[0] * Bk[3] - Bk[1] * Bk[2];
+            Bi[0] = Bk[3] / det;
+            Bi[1] = -Bk[1] / det;
+            Bi[2] = -Bk[2] / det;
+            Bi[3] = Bk[0] / det;
+        } else {
+            det = Bk[0] * (Bk[4] * Bk[8] - Bk[5] * Bk[7]) - Bk[1] * (Bk[3] * Bk[8] - Bk[5] * Bk[6]) +
+                  Bk[2] * (Bk[3] * Bk[7] - Bk[4] * Bk[6]);
+            Bi[0] = (Bk[4] * Bk[8] - Bk[5] * Bk[7]) / det;
+            Bi[1] = (Bk[2] * Bk[7] - Bk[1] * Bk[8]) / det;
+            Bi[2] = (Bk[1] * Bk[5] - Bk[2] * Bk[4]) / det;
+            Bi[3] = (Bk[5] * Bk[6] - Bk[3] * Bk[8]) / det;
+            Bi[4] = (Bk[0] * Bk[8] - Bk[2] * Bk[6]) / det;
+            Bi[5] = (Bk[2] * Bk[3] - Bk[0] * Bk[5]) / det;
+            Bi[6] = (Bk[3] * Bk[7] - Bk[4] * Bk[6]) / det;
+            Bi[7] = (Bk[1] * Bk[6] - Bk[0] * Bk[7]) / det;
+            Bi[8] = (Bk[0] * Bk[4] - Bk[1] * Bk[3]) / det;
+        }
+        if (!(det > 0.0) || !isfinite(det)) {  // not positive definite: no scaling of this node
+#pragma unroll
+            for (int c = 0; c < D * D; ++c) Bi[c] = (c % (D + 1) == 0) ? 1.0 : 0.0;
+        }
+        double rv[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            rv[i] = fr[i] ? -a.R[nd * D + i] : 0.0;
+            bb += rv[i] * rv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double zi = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) zi += Bi[i * D + k] * rv[k];
+            zi = fr[i] ? zi : 0.0;
+            a.r[nd * D + i] = rv[i];
+            a.z[nd * D + i] = zi;
+            a.p[nd * D + i] = zi;
+            a.x[nd * D + i] = 0.0;
+            rz0 += rv[i] * zi;
+        }
+#pragma unroll
+        for (int c = 0; c < D * D; ++c) a.minv[nd * D * D + c] = Bi[c];
+    }
+    bb = block_sum(bb, sh);
+    rz0 = block_sum(rz0, sh);
+    if (threadIdx.x == 0) {
+        prr[blockIdx.x] = bb;
+        prz[blockIdx.x] = rz0;
+    }
+    bool ok = grid_barrier(a.sync, nblk);
+    bb = grid_sum(prr, nblk, sh);
+    double rz = grid_sum(prz, nblk, sh);
+    double rr = bb;
+    int it = 0, status = 1;  // 1: not converged within max_iter
+    constexpr int LPR = D == 2 ? 8 : 16;  // lanes per row of the sparse product
+    const double tol2 = a.tol * a.tol * bb;
+    while (ok) {
+        if (rr <= tol2) {
+            status = 0;
+            break;
+        }
+        if (it >= a.max_iter) break;
+        // q = K p on the free rows (p vanishes on the prescribed DOFs)
+        double pq = 0.0;
+        {
+            // a warp takes 32 / LPR consecutive rows, LPR lanes per row; the
+            // loop bound is the same for all lanes of a warp (full-warp shuffles)
+            constexpr int RPW = 32 / LPR;
+            const int lane = threadIdx.x & 31, sub = lane % LPR;
+            for (int64_t r0 = (tid >> 5) * RPW; r0 < a.n_dof; r0 += (nth >> 5) * RPW) {
+                const int64_t row = r0 + lane / LPR;
+                double v = 0.0;
+                if (row < a.n_dof && a.free_mask[row]) {
+                    const int32_t b0 = a.rowp[row], b1 = a.rowp[row + 1];
+                    for (int32_t e = b0 + sub; e < b1; e += LPR) v += a.K[e] * __ldcg(a.p + a.col[e]);
+                }
+#pragma unroll
+                for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, LPR);
+                if (sub == 0 && row < a.n_dof) {
+                    a.q[row] = v;
+                    pq += v * __ldcg(a.p + row);
+                }
+            }
+        }
+        pq = block_sum(pq, sh);
+        if (threadIdx.x == 0) ppq[blockIdx.x] = pq;
+        if (!(ok = grid_barrier(a.sync, nblk))) break;
+        pq = grid_sum(ppq, nblk, sh);
+        if (!(pq > 0.0)) {  // K not positive definite on the search direction
+            status = 2;
+            break;
+        }
+        const double alpha = rz / pq;
+        double rzn = 0.0, rrn = 0.0;
+        for (int64_t nd = tid; nd < a.n_nodes; nd += nth) {
+            double rv[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int64_t k = nd * D + i;
+                a.x[k] += alpha * a.p[k];
+                rv[i] = a.r[k] - alpha * __ldcg(a.q + k);
+                a.r[k] = rv[i];
+                rrn += rv[i] * rv[i];
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                double zi = 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) zi += a.minv[nd * D * D + i * D + k] * rv[k];
+                zi = a.free_mask[nd * D + i] ? zi : 0.0;
+                a.z[nd * D + i] = zi;
+                rzn += rv[i] * zi;
+            }
+        }
+        rzn = block_sum(rzn, sh);
+        rrn = block_sum(rrn, sh);
+        if (threadIdx.x == 0) {
+            prz[blockIdx.x] = rzn;
+            prr[blockIdx.x] = rrn;
+        }
+        if (!(ok = grid_barrier(a.sync, nblk))) break;
+        rzn = grid_sum(prz, nblk, sh);
+        rr = grid_sum(prr, nblk, sh);
+        ++it;
+        if (rr <= tol2) continue;  // converged: x is final, p is not needed
+        const double beta = rzn / rz;
+        rz = rzn;
+        for (int64_t nd = tid; nd < a.n_nodes; nd += nth)
+#pragma unroll
+            for (int i = 0; i < D; ++i) a.p[nd * D + i] = a.z[nd * D + i] + beta * a.p[nd * D + i];
+        ok = grid_barrier(a.sync, nblk);
+    }
+    if (!ok) status = 5;
+    // outputs: du = x, u += x (each node by the thread that updated its x)
+    for (int64_t nd = tid; nd < a.n_nodes; nd += nth)
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int64_t k = nd * D + i;
+            const double v = a.x[k];
+            a.du[k] = v;
+            if (a.u) a.u[k] += v;
+        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.info[0] = (double)it;
+        a.info[1] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+        a.info[2] = (double)status;
+    }
+}
+
+bool solve_setup(rverom_mesh_s *m, const std::vector<int32_t> &rowp32, const std::vector<int32_t> &dpos) {
+    const int d = m->dim;
+    int occ = 0;
+    cudaError_t e = m->dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<2>, SOLVE_THREADS, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<3>, SOLVE_THREADS, 0);
+    if (e != cudaSuccess || occ < 1) return false;
+    m->solve_blocks = m->n_sm * (occ < 2 ? occ : 2);
+    const size_t nw = (size_t)m->n_dof * 5 + (size_t)m->n_nodes * d * d;
+    return cudaMalloc(&m->rowp, rowp32.size() * 4) == cudaSuccess &&
+           cudaMalloc(&m->colv, m->col.size() * 4) == cudaSuccess &&
+           cudaMalloc(&m->dpos, dpos.size() * 4) == cudaSuccess && cudaMalloc(&m->work, nw * 8) == cudaSuccess &&
+           cudaMalloc(&m->part, (size_t)3 * m->solve_blocks * 8) == cudaSuccess &&
+           cudaMalloc(&m->sync, 4 * sizeof(unsigned)) == cudaSuccess &&
+           cudaMemcpy(m->rowp, rowp32.data(), rowp32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(m->colv, m->col.data(), m->col.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(m->dpos, dpos.data(), dpos.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int macro_solve(rverom_mesh_t m, const double *Kvals, const double *R, const uint8_t *free_mask,
+                           double tol, int32_t max_iter, double *u, double *du, double *info, void *stream) {
+    if (!m || !Kvals || !R || !free_mask || !du || !info || !(tol >= 0.0) || max_iter < 0) return RVEROM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(m->sync, 0, 4 * sizeof(unsigned), st) != cudaSuccess) return RVEROM_ERR_CUDA;
+    SolveArgs a;
+    a.n_nodes = m->n_nodes;
+    a.n_dof = m->n_dof;
+    a.rowp = m->rowp;
+    a.col = m->colv;
+    a.dpos = m->dpos;
+    a.K = Kvals;
+    a.R = R;
+    a.free_mask = free_mask;
+    a.u = u;
+    a.du = du;
+    a.info = info;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.r = m->work;
+    a.z = a.r + m->n_dof;
+    a.p = a.z + m->n_dof;
+    a.q = a.p + m->n_dof;
+    a.x = a.q + m->n_dof;
+    a.minv = a.x + m->n_dof;
+    a.part = m->part;
+    a.sync = m->sync;
+    // cooperative launch: every block is resident, so the grid barriers are
+    // safe (and bounded in time all the same)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)m->solve_blocks);
+    cfg.blockDim = dim3(SOLVE_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = m->dim == 2 ? cudaLaunchKernelEx(&cfg, k_pcg<2>, a) : cudaLaunchKernelEx(&cfg, k_pcg<3>, a);
+    return e == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
 }

@@ -57,3 +57,31 @@ def plate_with_hole(nr, nt, half=1.0, radius=0.2):
         for i in range(nr):
             conn.append([ids[i, t], ids[i + 1, t], ids[i + 1, t1], ids[i, t1]])
     return X, np.array(conn, dtype=np.int64)
+
+
+def boundary_dofs(kind, X):
+    """Prescribed DOFs (node * d + i) of the synthetic macro problems, by
+    geometry only:
+      rect   left edge u_x, bottom edge u_y, right edge u_x (uniaxial tension)
+      plate  the normal displacement of the outer square's edges (biaxial)
+      box    every DOF of the face x = 0 (clamped) and u_z of the face x = L
+             (tip shear of a cantilever)
+    Returns (dofs, react_dofs) as int64 arrays: react_dofs are the DOFs whose
+    internal forces sum to the reaction of the loaded boundary."""
+    d = X.shape[1]
+    lo, hi = X.min(0), X.max(0)
+    on = lambda k, v: np.nonzero(np.isclose(X[:, k], v))[0]
+    if kind == 'rect':
+        left, bottom, right = on(0, lo[0]), on(1, lo[1]), on(0, hi[0])
+        dofs = np.concatenate([left * d, bottom * d + 1, right * d])
+        react = right * d
+    elif kind == 'plate':
+        xs = np.concatenate([on(0, lo[0]), on(0, hi[0])])
+        ys = np.concatenate([on(1, lo[1]), on(1, hi[1])])
+        dofs = np.concatenate([xs * d, ys * d + 1])
+        react = on(0, hi[0]) * d
+    else:
+        clamp, tip = on(0, lo[0]), on(0, hi[0])
+        dofs = np.concatenate([clamp * d + i for i in range(d)] + [tip * d + 2])
+        react = tip * d + 2
+    return np.unique(dofs).astype(np.int64), np.unique(react).astype(np.int64)
