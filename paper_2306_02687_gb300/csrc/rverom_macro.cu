@@ -26,8 +26,8 @@ struct rverom_mesh_s {
     int32_t *rowp = nullptr;     // device [n_dof + 1]
     int32_t *colv = nullptr;     // device [nnz]
     int32_t *dpos = nullptr;     // device [n_dof]: index of entry (node d + i, node d) in row node d + i
-    double *work = nullptr;      // device: r, z, p, q, x [n_dof] each; block inverses [n_nodes][d][d]
-    double *part = nullptr;      // device [3][solve_blocks] per-block partial sums
+    double *work = nullptr;      // device: r, u, p, s, x [n_dof] each; block inverses [n_nodes][d][d]; w [n_dof]
+    double *part = nullptr;      // device [2][3][solve_blocks] per-block partial sums (double-buffered)
     unsigned *sync = nullptr;    // device [4]: grid-barrier count and generation, error flag
     int solve_blocks = 0;
 };
@@ -373,11 +373,11 @@ extern "C" int macro_residual_norms(rverom_mesh_t m, const double *R, const uint
 // ones), the Newton correction of the monolithic scheme (Sec. 2, Eq. 6 and
 // its linearization; the paper solves it with a direct solver).  Conjugate
 // gradients preconditioned by the inverse nodal d x d diagonal blocks of K,
-// in one persistent cooperative kernel: every block owns a slice of the
-// nodes and rows, and three grid barriers per iteration separate the sparse
-// product, the update and the next search direction.  Dot products are
-// reduced per block and summed by every block in the same order, so that
-// all blocks take the same convergence decision.
+// in one persistent cooperative kernel (up to one block per SM): every block owns a
+// slice of the nodes and rows; per iteration, two grid barriers separate the
+// node-wise update from the sparse product and the sparse product from the
+// combined reduction.  Dot products are reduced per block and summed by every
+// block in the same order, so that all blocks take the same decisions.
 namespace {
 
 constexpr int SOLVE_THREADS = 256;
@@ -433,36 +433,69 @@ __device__ double block_sum(double v, double *sh) {
     if (l == 0) sh[w] = v;
     __syncthreads();
     double t = 0.0;
+#pragma unroll
     for (int k = 0; k < SOLVE_THREADS / 32; ++k) t += sh[k];
     return t;
 }
 
-// sum of the per-block partials (written by other blocks: read past L1),
-// the same order in every block
-__device__ double grid_sum(const double *part, unsigned nblk, double *sh) {
-    double v = 0.0;
-    if (threadIdx.x < 32)
-        for (unsigned b = threadIdx.x; b < nblk; b += 32) v += __ldcg(part + b);
-    if (threadIdx.x < 32) {
+// sums of the per-block partials of NV quantities (written by other blocks:
+// read past L1), one partial per thread and the same order in every block
+template <int NV>
+__device__ void grid_sums(const double *part, unsigned nblk, double *sh, double (&out)[NV]) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int k = 0; k < NV; ++k) {
+        double v = threadIdx.x < nblk ? __ldcg(part + k * nblk + threadIdx.x) : 0.0;
+        out[k] = block_sum(v, sh + 8 * k);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) sh[8] = v;
-    __syncthreads();
-    return sh[8];
 }
 
 template <int D>
+__device__ __forceinline__ void apply_minv(const double *minv, int64_t nd, const double (&rv)[D], const uint8_t *fm,
+                                           double (&zv)[D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        double zi = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) zi += minv[nd * D * D + i * D + k] * rv[k];
+        zv[i] = fm[nd * D + i] ? zi : 0.0;
+    }
+}
+
+// Preconditioned conjugate gradients in the single-reduction form of
+// Chronopoulos and Gear: per iteration one sparse product w = K u and one
+// combined reduction of (r, u), (w, u), (r, r), so two grid barriers.
+template <int D>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg(SolveArgs a) {
-    __shared__ double sh[16];
+    __shared__ double sh[32];
     const unsigned nblk = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)nblk * blockDim.x;
-    double *ppq = a.part, *prz = a.part + nblk, *prr = a.part + 2 * nblk;
+    double *s_ = a.q;  // s = K p
+    double *wv = a.minv + a.n_nodes * D * D;  // w = K u  [n_dof]
+    constexpr int LPR = D == 2 ? 8 : 16;       // lanes per row of the sparse product
+    constexpr int RPW = 32 / LPR;
+    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    // sparse product w = K u on the free rows (u vanishes on the prescribed
+    // DOFs) with the partial (w, u); a warp takes RPW consecutive rows
+    auto spmv = [&](double &wu) {
+        for (int64_t r0 = (tid >> 5) * RPW; r0 < a.n_dof; r0 += (nth >> 5) * RPW) {
+            const int64_t row = r0 + lane / LPR;
+            double v = 0.0;
+            if (row < a.n_dof && a.free_mask[row]) {
+                const int32_t b0 = a.rowp[row], b1 = a.rowp[row + 1];
+                for (int32_t e = b0 + sub; e < b1; e += LPR) v += a.K[e] * __ldcg(a.z + a.col[e]);
+            }
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, LPR);
+            if (sub == 0 && row < a.n_dof) {
+                wv[row] = v;
+                wu += v * __ldcg(a.z + row);
+            }
+        }
+    };
     // preconditioner: inverse of each node's diagonal block with the rows and
     // columns of prescribed DOFs replaced by the identity; b = -R on the free
-    // DOFs; x = 0, r = b, z = M r, p = z
-    double bb = 0.0, rz0 = 0.0;
+    // DOFs; x = 0, r = b, u = M r (stored in z), p = s = 0
+    double bb = 0.0, ru = 0.0;
     for (int64_t nd = tid; nd < a.n_nodes; nd += nth) {
         double Bk[D * D], Bi[D * D];
         bool fr[D];
@@ -497,39 +530,44 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg(SolveArgs a) {
 #pragma unroll
             for (int c = 0; c < D * D; ++c) Bi[c] = (c % (D + 1) == 0) ? 1.0 : 0.0;
         }
-        double rv[D];
+#pragma unroll
+        for (int c = 0; c < D * D; ++c) a.minv[nd * D * D + c] = Bi[c];
+        double rv[D], uv[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             rv[i] = fr[i] ? -a.R[nd * D + i] : 0.0;
             bb += rv[i] * rv[i];
         }
+        apply_minv<D>(a.minv, nd, rv, a.free_mask, uv);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            double zi = 0.0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) zi += Bi[i * D + k] * rv[k];
-            zi = fr[i] ? zi : 0.0;
-            a.r[nd * D + i] = rv[i];
-            a.z[nd * D + i] = zi;
-            a.p[nd * D + i] = zi;
-            a.x[nd * D + i] = 0.0;
-            rz0 += rv[i] * zi;
+            const int64_t k = nd * D + i;
+            a.r[k] = rv[i];
+            a.z[k] = uv[i];
+            a.p[k] = 0.0;
+            s_[k] = 0.0;
+            a.x[k] = 0.0;
+            ru += rv[i] * uv[i];
         }
-#pragma unroll
-        for (int c = 0; c < D * D; ++c) a.minv[nd * D * D + c] = Bi[c];
     }
-    bb = block_sum(bb, sh);
-    rz0 = block_sum(rz0, sh);
-    if (threadIdx.x == 0) {
-        prr[blockIdx.x] = bb;
-        prz[blockIdx.x] = rz0;
+    bool ok = grid_barrier(a.sync, nblk);  // u complete
+    double wu = 0.0;
+    if (ok) spmv(wu);
+    {
+        const double b1 = block_sum(bb, sh), b2 = block_sum(ru, sh + 8), b3 = block_sum(wu, sh + 16);
+        if (threadIdx.x == 0) {
+            a.part[blockIdx.x] = b2;             // (r, u)
+            a.part[nblk + blockIdx.x] = b3;      // (w, u)
+            a.part[2 * nblk + blockIdx.x] = b1;  // (r, r)
+        }
     }
-    bool ok = grid_barrier(a.sync, nblk);
-    bb = grid_sum(prr, nblk, sh);
-    double rz = grid_sum(prz, nblk, sh);
-    double rr = bb;
+    ok = ok && grid_barrier(a.sync, nblk);
+    double sums[3] = {0.0, 0.0, 0.0};
+    if (ok) grid_sums<3>(a.part, nblk, sh, sums);
+    double gam = sums[0], del = sums[1];
+    bb = sums[2];
+    double rr = bb, alpha = gam / del, beta = 0.0;
     int it = 0, status = 1;  // 1: not converged within max_iter
-    constexpr int LPR = D == 2 ? 8 : 16;  // lanes per row of the sparse product
     const double tol2 = a.tol * a.tol * bb;
     while (ok) {
         if (rr <= tol2) {
@@ -537,75 +575,54 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg(SolveArgs a) {
             break;
         }
         if (it >= a.max_iter) break;
-        // q = K p on the free rows (p vanishes on the prescribed DOFs)
-        double pq = 0.0;
-        {
-            // a warp takes 32 / LPR consecutive rows, LPR lanes per row; the
-            // loop bound is the same for all lanes of a warp (full-warp shuffles)
-            constexpr int RPW = 32 / LPR;
-            const int lane = threadIdx.x & 31, sub = lane % LPR;
-            for (int64_t r0 = (tid >> 5) * RPW; r0 < a.n_dof; r0 += (nth >> 5) * RPW) {
-                const int64_t row = r0 + lane / LPR;
-                double v = 0.0;
-                if (row < a.n_dof && a.free_mask[row]) {
-                    const int32_t b0 = a.rowp[row], b1 = a.rowp[row + 1];
-                    for (int32_t e = b0 + sub; e < b1; e += LPR) v += a.K[e] * __ldcg(a.p + a.col[e]);
-                }
-#pragma unroll
-                for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, LPR);
-                if (sub == 0 && row < a.n_dof) {
-                    a.q[row] = v;
-                    pq += v * __ldcg(a.p + row);
-                }
-            }
-        }
-        pq = block_sum(pq, sh);
-        if (threadIdx.x == 0) ppq[blockIdx.x] = pq;
-        if (!(ok = grid_barrier(a.sync, nblk))) break;
-        pq = grid_sum(ppq, nblk, sh);
-        if (!(pq > 0.0)) {  // K not positive definite on the search direction
+        if (!(del > 0.0) || !(gam > 0.0) || !isfinite(alpha) || !(alpha > 0.0)) {  // K not positive definite
             status = 2;
             break;
         }
-        const double alpha = rz / pq;
-        double rzn = 0.0, rrn = 0.0;
+        // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M r
+        double pr = 0.0, prr = 0.0;
         for (int64_t nd = tid; nd < a.n_nodes; nd += nth) {
-            double rv[D];
+            double rv[D], uv[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 const int64_t k = nd * D + i;
-                a.x[k] += alpha * a.p[k];
-                rv[i] = a.r[k] - alpha * __ldcg(a.q + k);
+                const double pk = a.z[k] + beta * a.p[k];
+                const double sk = __ldcg(wv + k) + beta * s_[k];
+                a.p[k] = pk;
+                s_[k] = sk;
+                a.x[k] += alpha * pk;
+                rv[i] = a.r[k] - alpha * sk;
                 a.r[k] = rv[i];
-                rrn += rv[i] * rv[i];
+                prr += rv[i] * rv[i];
             }
+            apply_minv<D>(a.minv, nd, rv, a.free_mask, uv);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                double zi = 0.0;
-#pragma unroll
-                for (int k = 0; k < D; ++k) zi += a.minv[nd * D * D + i * D + k] * rv[k];
-                zi = a.free_mask[nd * D + i] ? zi : 0.0;
-                a.z[nd * D + i] = zi;
-                rzn += rv[i] * zi;
+                a.z[nd * D + i] = uv[i];
+                pr += rv[i] * uv[i];
             }
         }
-        rzn = block_sum(rzn, sh);
-        rrn = block_sum(rrn, sh);
+        double *pt = a.part + (size_t)((it + 1) & 1) * 3 * nblk;  // partials of this iteration (double-buffered)
+        pr = block_sum(pr, sh);
+        prr = block_sum(prr, sh + 8);
         if (threadIdx.x == 0) {
-            prz[blockIdx.x] = rzn;
-            prr[blockIdx.x] = rrn;
+            pt[blockIdx.x] = pr;
+            pt[2 * nblk + blockIdx.x] = prr;
         }
-        if (!(ok = grid_barrier(a.sync, nblk))) break;
-        rzn = grid_sum(prz, nblk, sh);
-        rr = grid_sum(prr, nblk, sh);
+        if (!(ok = grid_barrier(a.sync, nblk))) break;  // u complete
+        double pwu = 0.0;
+        spmv(pwu);
+        pwu = block_sum(pwu, sh + 16);
+        if (threadIdx.x == 0) pt[nblk + blockIdx.x] = pwu;
+        if (!(ok = grid_barrier(a.sync, nblk))) break;  // partials complete
+        grid_sums<3>(pt, nblk, sh, sums);
         ++it;
-        if (rr <= tol2) continue;  // converged: x is final, p is not needed
-        const double beta = rzn / rz;
-        rz = rzn;
-        for (int64_t nd = tid; nd < a.n_nodes; nd += nth)
-#pragma unroll
-            for (int i = 0; i < D; ++i) a.p[nd * D + i] = a.z[nd * D + i] + beta * a.p[nd * D + i];
-        ok = grid_barrier(a.sync, nblk);
+        rr = sums[2];
+        const double gn = sums[0];
+        del = sums[1];
+        beta = gn / gam;
+        gam = gn;
+        alpha = gn / (del - beta * gn / alpha);
     }
     if (!ok) status = 5;
     // outputs: du = x, u += x (each node by the thread that updated its x)
@@ -630,12 +647,20 @@ bool solve_setup(rverom_mesh_s *m, const std::vector<int32_t> &rowp32, const std
     cudaError_t e = m->dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<2>, SOLVE_THREADS, 0)
                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<3>, SOLVE_THREADS, 0);
     if (e != cudaSuccess || occ < 1) return false;
-    m->solve_blocks = m->n_sm * (occ < 2 ? occ : 2);
-    const size_t nw = (size_t)m->n_dof * 5 + (size_t)m->n_nodes * d * d;
+    // blocks: about 4096 non-zeros of K each (an iteration is latency-bound:
+    // fewer blocks make the grid barriers cheaper, more make the sparse
+    // product shorter), between 8 and one per SM, at most SOLVE_THREADS (one
+    // partial per thread in grid_sums)
+    int64_t nb = m->nnz / 4096;
+    if (nb > m->n_sm) nb = m->n_sm;
+    if (nb > SOLVE_THREADS) nb = SOLVE_THREADS;
+    if (nb < 8) nb = 8;
+    m->solve_blocks = (int)nb;
+    const size_t nw = (size_t)m->n_dof * 6 + (size_t)m->n_nodes * d * d;
     return cudaMalloc(&m->rowp, rowp32.size() * 4) == cudaSuccess &&
            cudaMalloc(&m->colv, m->col.size() * 4) == cudaSuccess &&
            cudaMalloc(&m->dpos, dpos.size() * 4) == cudaSuccess && cudaMalloc(&m->work, nw * 8) == cudaSuccess &&
-           cudaMalloc(&m->part, (size_t)3 * m->solve_blocks * 8) == cudaSuccess &&
+           cudaMalloc(&m->part, (size_t)6 * m->solve_blocks * 8) == cudaSuccess &&
            cudaMalloc(&m->sync, 4 * sizeof(unsigned)) == cudaSuccess &&
            cudaMemcpy(m->rowp, rowp32.data(), rowp32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
            cudaMemcpy(m->colv, m->col.data(), m->col.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
