@@ -242,7 +242,7 @@ int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_m
  * and columns of prescribed DOFs replaced by the identity), in the
  * single-reduction form of Chronopoulos and Gear; stops when
  * ||r||_2 <= tol ||R_free||_2 or after max_iter iterations.  Runs as one
- * cooperative kernel (8 blocks up to one per SM, by the size of K, in the mesh's workspace:
+ * cooperative kernel (one block per SM, in the mesh's workspace:
  * no allocation, so the call can sit in a CUDA graph with the rest of the
  * Newton iteration).  Calls on one mesh must not overlap.
  * Device arrays: Kvals [nnz] (CSR of macro_mesh_csr), R [n_dof],
