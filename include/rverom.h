@@ -253,6 +253,45 @@ int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_m
 int macro_solve(rverom_mesh_t m, const double *Kvals, const double *R, const uint8_t *free_mask, double tol,
                 int32_t max_iter, double *u, double *du, double *info, void *stream);
 
+/* Biot and Cauchy outputs for updated-Lagrangian macro codes (Sec. 3.2.2,
+ * Eqs. workconjugacy and biotstress; Appendix A), from the homogenized
+ * first Piola-Kirchhoff stress and its tangent at n points (Fbar = R U):
+ *   biot    [n][ns]      T = sym(R^T Pbar), work conjugate to U
+ *   cbiot   [n][ns][ns]  dT_v / dU_w for symmetric stretch variations at
+ *                        fixed R (dFbar = R dU)
+ *   sigma   [n][ns]      Cauchy stress from T = (J/2)(R^T sigma F^-T +
+ *                        F^-1 sigma R), solved for the symmetric sigma
+ *   csigma  [n][ns][ns]  dsigma_v / dD_w ~ (dsigma/dT) C^B sym(R^T D F), the
+ *                        constant-rotation approximation of Appendix A
+ * Symmetric tensors by their ns tensor components (the project's order);
+ * derivatives with respect to a shear component move both of its entries.
+ * Device arrays; Fbar [n][g], Pbar [n][g], dPdF [n][g][g] (as written by
+ * rve_rom_eval_batch); any of the four outputs may be NULL.  Points with
+ * det Fbar <= 0 or a singular map get NaN outputs. */
+int rve_rom_biot_cauchy(int32_t dim, int64_t n, const double *Fbar, const double *Pbar, const double *dPdF,
+                        double *biot, double *cbiot, double *sigma, double *csigma, void *stream);
+
+/* Clustered training (Sec. 3.4, Box 2), step 1: the linear-elastic
+ * surrogate with the initial RVE stiffness C0 (device [g][g], e.g. the
+ * condensed tangent dPbar/dFbar of the hyper-ROM at Fbar = I):
+ * Pbar = C0 (Fbar - I) and dPdF = C0 (may be NULL) at n points. */
+int surrogate_linear_eval(int32_t dim, int64_t n, const double *C0, const double *Fbar, double *Pbar,
+                          double *dPdF, void *stream);
+
+/* Clustered training (Box 2), step 3: k-means (Lloyd) of n macro paths
+ * X [n][dim] (device; e.g. the displacement gradients of every macro point
+ * over the load steps of a surrogate run, concatenated).  centers [k][dim]
+ * (device) holds the initial centres on entry and the final ones on return;
+ * labels [n] (device, out) the nearest centre of every path (squared
+ * Euclidean distance summed over the coordinates in order; ties to the
+ * lowest index).  Iterates assignment and update (mean of the assigned
+ * paths; an empty cluster keeps its centre) until no label changes or
+ * max_iter updates.  info [2] (host, out): updates done, final sum of
+ * squared distances.  Synchronous; allocates a few bytes of device
+ * scratch per call (an offline step). */
+int paths_kmeans(int64_t n, int32_t dim, const double *X, int32_t k, double *centers, int32_t *labels,
+                 int32_t max_iter, double *info, void *stream);
+
 /* ---- diagnostics (no counterpart in the paper) -------------------------- */
 
 /* The double-float natural logarithm that the mixed form's micro law uses

@@ -85,6 +85,8 @@ def kmeans(X, C_init, max_iter=100):
             sel = labels == c
             if sel.any():
                 C[c] = X[sel].mean(axis=0)
+    else:                                   # out of iterations: labels of the final centres
+        labels = assign(X, C)[0]
     _, dist = assign(X, C)
     inertia = dist[np.arange(len(X)), labels].sum()
     return C, labels, it, inertia, hist

@@ -286,6 +286,48 @@ def macro_solve(m, Kvals, R, free_mask, u=None, du=None, info=None, tol=1e-12, m
     return du, info
 
 
+def rve_rom_biot_cauchy(Fbar, Pbar, dPdF, biot=None, cbiot=None, sigma=None, csigma=None, stream=None):
+    """Biot stress and tangent, Cauchy stress and its approximate tangent of
+    every point (Sec. 3.2.2, Appendix A); returns the four output tensors."""
+    n, g = Fbar.shape
+    dim = 2 if g == 4 else 3
+    ns = 3 if dim == 2 else 6
+    dev = Fbar.device
+    mk = lambda x, shp: torch.empty(shp, dtype=torch.float64, device=dev) if x is None else x
+    biot, sigma = mk(biot, (n, ns)), mk(sigma, (n, ns))
+    cbiot, csigma = mk(cbiot, (n, ns, ns)), mk(csigma, (n, ns, ns))
+    _native.check(_native.lib().rve_rom_biot_cauchy(
+        dim, n, _ptr(Fbar, torch.float64, (n, g), 'Fbar'), _ptr(Pbar, torch.float64, (n, g), 'Pbar'),
+        _ptr(dPdF, torch.float64, (n, g, g), 'dPdF'), _ptr(biot, torch.float64, (n, ns), 'biot'),
+        _ptr(cbiot, torch.float64, (n, ns, ns), 'cbiot'), _ptr(sigma, torch.float64, (n, ns), 'sigma'),
+        _ptr(csigma, torch.float64, (n, ns, ns), 'csigma'), _stream(stream)), 'rve_rom_biot_cauchy')
+    return biot, cbiot, sigma, csigma
+
+
+def surrogate_linear_eval(C0, Fbar, Pbar, dPdF=None, stream=None):
+    """Linear-elastic surrogate Pbar = C0 (Fbar - I), dPdF = C0 (Box 2, step 1)."""
+    n, g = Fbar.shape
+    _native.check(_native.lib().surrogate_linear_eval(
+        2 if g == 4 else 3, n, _ptr(C0, torch.float64, (g, g), 'C0'), _ptr(Fbar, torch.float64, (n, g), 'Fbar'),
+        _ptr(Pbar, torch.float64, (n, g), 'Pbar'),
+        _ptr(dPdF, torch.float64, (n, g, g), 'dPdF') if dPdF is not None else None, _stream(stream)),
+        'surrogate_linear_eval')
+
+
+def paths_kmeans(X, centers, max_iter=200, labels=None, stream=None):
+    """k-means of the rows of X (device [n][dim]) from the given centres
+    (updated in place); returns (labels, updates done, inertia)."""
+    n, dim = X.shape
+    k = centers.shape[0]
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=X.device)
+    info = (ctypes.c_double * 2)()
+    _native.check(_native.lib().paths_kmeans(
+        n, dim, _ptr(X, torch.float64, (n, dim), 'X'), k, _ptr(centers, torch.float64, (k, dim), 'centers'),
+        _ptr(labels, torch.int32, (n,), 'labels'), int(max_iter), info, _stream(stream)), 'paths_kmeans')
+    return labels, int(info[0]), info[1]
+
+
 def rverom_df_log(x, out, stream=None):
     """The library's double-float logarithm at the points of x (float64, CUDA)."""
     n = x.shape[0]

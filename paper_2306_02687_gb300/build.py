@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(HERE, 'librverom.so')
-SOURCES = ['rverom_eval.cu', 'rverom_adjoint.cu', 'rverom_macro.cu', 'rverom_adjoint_static.cu', 'rverom_diag.cu']
+SOURCES = ['rverom_eval.cu', 'rverom_adjoint.cu', 'rverom_macro.cu', 'rverom_adjoint_static.cu', 'rverom_diag.cu',
+           'rverom_train.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC']
 
