@@ -59,17 +59,24 @@ def zero_state(rom):
                 Uprev=np.zeros(rom.ns))
 
 
-def reduced_system(rom, U, q):
-    """a2-a5: returns r, V0*Pbar_U (g), K, K_qF, K_FF, F_i, status."""
+def reduced_system(rom, U, q, pointwise=None):
+    """a2-a5: returns r, V0*Pbar_U (g), K, K_qF, K_FF, F_i, status.
+    pointwise(F [m, d, d]) -> (P [m, d, d], A [m, g, g]) replaces the
+    Neo-Hooke law (a history-dependent law at the ECM points)."""
     d, g, m = rom.d, rom.g, rom.m
     F = U.reshape(1, g) + np.einsum('icj,j->ic', rom.B, q)
     F = F.reshape(m, d, d)
     if np.any(np.linalg.det(F) <= 0.0):
         return None, None, None, None, None, F, DETF_NONPOS
-    mu = rom.moduli[rom.phase, 0]
-    ka = rom.moduli[rom.phase, 1]
-    P = law.stress(F, mu, ka).reshape(m, g)
-    A = law.tangent(F, mu, ka).reshape(m, g, g)
+    if pointwise is None:
+        mu = rom.moduli[rom.phase, 0]
+        ka = rom.moduli[rom.phase, 1]
+        P = law.stress(F, mu, ka).reshape(m, g)
+        A = law.tangent(F, mu, ka).reshape(m, g, g)
+    else:
+        P, A = pointwise(F)
+        P = P.reshape(m, g)
+        A = A.reshape(m, g, g)
     wP = rom.w[:, None] * P
     r = np.einsum('icj,ic->j', rom.B, wP)
     VPU = wP.sum(0)
@@ -83,7 +90,7 @@ def reduced_system(rom, U, q):
     return r, VPU, K, KqF, KFF, F, OK
 
 
-def eval_point(rom, Fbar, q, s, S, Uprev):
+def eval_point(rom, Fbar, q, s, S, Uprev, pointwise=None):
     """One monolithic evaluation (steps a1-a7).  Returns a dict with Pbar
     (d x d), dPdF (g x g, [out, in] in row-major component order), the new
     state q, s, S, Uprev, rnorm = max|r| and status."""
@@ -92,7 +99,7 @@ def eval_point(rom, Fbar, q, s, S, Uprev):
     R, U = pol.polar(Fbar)
     Uv = rvemod.to_voigt(U)
     q = q - s - S @ (Uv - Uprev)
-    r, VPU, K, KqF, KFF, F, st = reduced_system(rom, U, q)
+    r, VPU, K, KqF, KFF, F, st = reduced_system(rom, U, q, pointwise)
     out = dict(q=q, status=st)
     if st != OK:
         return out
