@@ -253,6 +253,31 @@ int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_m
 int macro_solve(rverom_mesh_t m, const double *Kvals, const double *R, const uint8_t *free_mask, double tol,
                 int32_t max_iter, double *u, double *du, double *info, void *stream);
 
+/* Largest m~ over the types of a handle (the ECM-point stride of the
+ * history arrays of rve_rom_eval_batch_j2). */
+int rve_rom_mmax(rverom_t h, int32_t *mmax);
+
+/* rve_rom_eval_batch with a history-dependent micro law (planar RVEs,
+ * n~ <= 32, float64): small-strain J2 plasticity with linear isotropic
+ * hardening at every ECM point, the matrix law of Example 1 (Sec. 5.1),
+ * under plane strain (radial return; the in-plane stress in the place of P,
+ * the in-plane block of the consistent tangent in the place of dP/dF).
+ * Phases use the handle's (mu, kappa) and, from `plastic` (host
+ * [n_types][2][2]), the yield stress sy0 and hardening modulus h of each
+ * phase; sy0 <= 0 or infinite makes the phase elastic.
+ * hist_in  [n][mmax][7] (device) records (plastic strain 11, 22, 33, 12, 13,
+ *          23 and equivalent plastic strain) of the last converged load
+ *          step; zero for a virgin material
+ * hist_out [n][mmax][7] (device, out; distinct from hist_in) the records
+ *          after this evaluation's return mappings; the caller copies them
+ *          to hist_in once the load step has converged
+ * Other arguments, outputs and status codes as rve_rom_eval_batch; failed
+ * points keep their state and their history. */
+int rve_rom_eval_batch_j2(rverom_t h, int64_t n_points, const int32_t *type, const double *Fbar, double *q,
+                          double *s, double *S, double *Uprev, const double *hist_in, double *hist_out,
+                          const double *plastic, double *Pbar, double *dPdF, double *rnorm, int32_t *status,
+                          void *stream);
+
 /* Biot and Cauchy outputs for updated-Lagrangian macro codes (Sec. 3.2.2,
  * Eqs. workconjugacy and biotstress; Appendix A), from the homogenized
  * first Piola-Kirchhoff stress and its tangent at n points (Fbar = R U):

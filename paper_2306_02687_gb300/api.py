@@ -286,6 +286,34 @@ def macro_solve(m, Kvals, R, free_mask, u=None, du=None, info=None, tol=1e-12, m
     return du, info
 
 
+def rve_rom_mmax(h):
+    """Largest number of ECM points over the types (history stride)."""
+    v = ctypes.c_int32()
+    _native.check(_native.lib().rve_rom_mmax(h.ptr, ctypes.byref(v)), 'rve_rom_mmax')
+    return v.value
+
+
+def rve_rom_eval_batch_j2(h, Fbar, q, s, S, Uprev, hist_in, hist_out, plastic, Pbar, dPdF, rnorm, status,
+                          type=None, stream=None):
+    """rve_rom_eval_batch with small-strain J2 plasticity at the ECM points
+    (planar RVEs): plastic [n_types][2][2] = (yield stress, hardening
+    modulus) per phase (yield <= 0 or inf: elastic); hist_in / hist_out
+    [n][mmax][7] device records (see include/rverom.h)."""
+    n = Fbar.shape[0]
+    g, ns, nm = h.g, h.ns, h.nmax
+    mm = rve_rom_mmax(h)
+    pl = np.ascontiguousarray(plastic, dtype=np.float64).reshape(h.n_types * 4)
+    args = [_ptr(type, torch.int32, (n,), 'type') if type is not None else None,
+            _ptr(Fbar, torch.float64, (n, g), 'Fbar'),
+            _ptr(q, torch.float64, (n, nm), 'q'), _ptr(s, torch.float64, (n, nm), 's'),
+            _ptr(S, torch.float64, (n, nm, ns), 'S'), _ptr(Uprev, torch.float64, (n, ns), 'Uprev'),
+            _ptr(hist_in, torch.float64, (n, mm, 7), 'hist_in'), _ptr(hist_out, torch.float64, (n, mm, 7), 'hist_out'),
+            pl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            _ptr(Pbar, torch.float64, (n, g), 'Pbar'), _ptr(dPdF, torch.float64, (n, g, g), 'dPdF'),
+            _ptr(rnorm, torch.float64, (n,), 'rnorm'), _ptr(status, torch.int32, (n,), 'status')]
+    _native.check(_native.lib().rve_rom_eval_batch_j2(h.ptr, n, *args, _stream(stream)), 'rve_rom_eval_batch_j2')
+
+
 def rve_rom_biot_cauchy(Fbar, Pbar, dPdF, biot=None, cbiot=None, sigma=None, csigma=None, stream=None):
     """Biot stress and tangent, Cauchy stress and its approximate tangent of
     every point (Sec. 3.2.2, Appendix A); returns the four output tensors."""
