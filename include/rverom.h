@@ -278,6 +278,34 @@ int rve_rom_eval_batch_j2(rverom_t h, int64_t n_points, const int32_t *type, con
                           const double *plastic, double *Pbar, double *dPdF, double *rnorm, int32_t *status,
                           void *stream);
 
+/* ---- offline (training) stage on the GPU, planar RVEs -------------------
+ * RVE: the unit cell (V0 = 1) meshed by n x n bilinear quadrilaterals with
+ * 2 x 2 Gauss points; element e = ix + n iy, node v = ix + n iy (periodic:
+ * indices mod n), micro integration point p = 4 e + gauss point (reference
+ * coordinates (xi_0, xi_1) in {-,+}^2, the second fastest); the periodic
+ * fluctuation w has DOFs v d + i, node 0 fixed, so the reduced vector of
+ * n_dof = 2 n^2 - 2 entries drops the first two; F = Fbar + grad w;
+ * compressible Neo-Hooke law per element phase (phase [n * n], moduli [2][2]
+ * (mu, kappa) host).  Every call below is asynchronous on `stream` unless it
+ * says otherwise. */
+
+/* Full-order snapshots (Sec. 3.2.1, Eq. snapshots_displacement): for each
+ * of n_paths training paths (one CTA per path), the micro equilibrium at
+ * the macro stretches paths [n_paths][n_steps][4] (device, row-major 2 x 2)
+ * in turn, each from the previous solution, by Newton's method
+ * (max|f| <= tol) with matrix-free block-Jacobi preconditioned conjugate
+ * gradients (relative tolerance cg_tol) for the corrections; the converged
+ * fluctuations are the rows X [n_paths * n_steps][n_dof] (device).
+ * linear = 1 instead solves the linearized RVE at Fbar = I for the three
+ * unit symmetric macro strains (n_paths = 3, n_steps ignored, paths may be
+ * NULL): w_v = -K_ww^-1 K_wF E_v, the elastic responses of Eq.
+ * SVD_displacement.  info [n_paths][4] (device): Newton iterations, CG
+ * iterations, final max|f|, status (0 ok, 1 det F <= 0, 2 CG breakdown,
+ * 3 Newton not converged).  Allocates its workspace with cudaMallocAsync. */
+int rve_snapshots(int32_t n, const int32_t *phase, const double *moduli, int32_t n_paths, int32_t n_steps,
+                  const double *paths, int32_t linear, double tol, double cg_tol, int32_t max_newton,
+                  int32_t max_cg, double *X, double *info, void *stream);
+
 /* Biot and Cauchy outputs for updated-Lagrangian macro codes (Sec. 3.2.2,
  * Eqs. workconjugacy and biotstress; Appendix A), from the homogenized
  * first Piola-Kirchhoff stress and its tangent at n points (Fbar = R U):

@@ -46,6 +46,8 @@ SIGNATURES = {
     'rve_rom_mmax': (c_int, [c_vp, P(c_int)]),
     'rve_rom_eval_batch_j2': (c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                       P(c_dbl), c_vp, c_vp, c_vp, c_vp, c_vp]),
+    'rve_snapshots': (c_int, [c_int, c_vp, P(c_dbl), c_int, c_int, c_vp, c_int, c_dbl, c_dbl, c_int, c_int,
+                              c_vp, c_vp, c_vp]),
     'rve_rom_biot_cauchy': (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'surrogate_linear_eval': (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'paths_kmeans': (c_int, [c_i64, c_int, c_vp, c_int, c_vp, c_vp, c_int, P(c_dbl), c_vp]),

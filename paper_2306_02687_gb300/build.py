@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, 'csrc')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(HERE, 'librverom.so')
 SOURCES = ['rverom_eval.cu', 'rverom_adjoint.cu', 'rverom_macro.cu', 'rverom_adjoint_static.cu', 'rverom_diag.cu',
-           'rverom_train.cu', 'rverom_j2.cu']
+           'rverom_train.cu', 'rverom_j2.cu', 'rverom_offline.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC']
 

@@ -127,7 +127,7 @@ def test_load_unload_is_irreversible():
     orom = reduced.Rom.load(rom_path('c1'))
     X, conn = meshes.rect(2, 2)
     prob = macro.uniaxial_problem(macro.MacroMesh(X, conn), 0.02)
-    lf = [0.5, 1.0, 0.5, 0.0]
+    lf = [0.5, 1.0, 0.8, 0.6, 0.4, 0.2, 0.0]      # unloading in small steps (monolithic predictor)
     plastic = np.array([[SY0, HK], [np.inf, 0.0]])
     res = j2.driver(prob, orom, plastic, lf)
     ela = j2.driver(prob, orom, np.array([[np.inf, 0.0], [np.inf, 0.0]]), lf)
