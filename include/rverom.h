@@ -306,6 +306,50 @@ int rve_snapshots(int32_t n, const int32_t *phase, const double *moduli, int32_t
                   const double *paths, int32_t linear, double tol, double cg_tol, int32_t max_newton,
                   int32_t max_cg, double *X, double *info, void *stream);
 
+/* POD with the elastic/inelastic split (Sec. 3.2.1, Eqs. SVD_displacement
+ * and snapshots_displacement): Phi rows 0 .. n_el-1 are the orthonormalized
+ * rows of W_el [n_el][n_dof] (the linearized responses; n_el <= 8), rows
+ * n_el .. n_modes-1 the leading left singular vectors of the snapshots
+ * X [n_snap][n_dof] with their W_el part removed, computed from the
+ * eigen-decomposition of their Gram matrix (cyclic Jacobi); eig [n_snap]
+ * the eigenvalues (squared singular values) in descending order; info [2]
+ * (device) Jacobi sweeps and final relative off-diagonal norm.  Device
+ * arrays; allocates scratch with cudaMallocAsync. */
+int pod_modes(int64_t n_dof, int32_t n_snap, const double *X, int32_t n_el, const double *W_el, int32_t n_modes,
+              double *Phi, double *eig, double *info, void *stream);
+
+/* Gradients of the modes Phi [n_modes][n_dof] at every micro integration
+ * point of the n x n RVE: B [n_ip][4][n_modes] (device), the gradient table
+ * of the fully integrated ROM (Gauss weights (1 / 2n)^2 each, V0 = 1). */
+int rve_mode_gradients(int32_t n, int32_t n_modes, const double *Phi, double *B, void *stream);
+
+/* The ECM training matrix of Sec. 3.3 (Eq. SVDlambda's x_f): for every
+ * training state s (stretch U [n_snap][4], converged amplitudes
+ * q [n_snap][n_modes] of the fully integrated ROM with table B) and micro
+ * point p the integrand f = [B_p^T P_p; P_p] (n_modes + 4 rows per state),
+ * minus its integral over the cell (V0 = 1) per row; then the mode rows and
+ * the stress rows each scaled to unit Frobenius norm.  xf
+ * [n_snap * (n_modes + 4)][n_ip] (device).  Synchronous; RVEROM_ERR_ARG if
+ * a state folds a micro point (det F <= 0). */
+int ecm_training_matrix(int32_t n, const int32_t *phase, const double *moduli, int32_t n_modes, const double *B,
+                        int32_t n_snap, const double *U, const double *q, double *xf, void *stream);
+
+/* Empirical cubature (Sec. 3.3, Eq. SVDlambda and Box 1): the leading
+ * m_target - 1 right singular vectors lambda of xf [n_rows][m] (device) by
+ * randomized subspace iteration from the Gaussian test matrix Omega
+ * [n_rows][k] (device, k >= m_target - 1; power_its power iterations,
+ * Cholesky-QR re-orthonormalization), then the greedy selection of Box 1 on
+ * J = [lambda 1]^T, b = [0 V0]^T: pick the available column most aligned
+ * with r = b - J_z w (ties to the lowest index), least-squares weights,
+ * non-negative least squares (Lawson-Hanson) when a weight is negative,
+ * zero-weight points dropped for good, until m_target points or no
+ * candidate is left.  z [m_target] (device int32) and w [m_target] (device)
+ * receive the points and weights, *n_sel (host) their count, info [4]
+ * (host): greedy iterations, final |J_z w - b|, least-squares solves, 0.
+ * m_target <= 1000.  Synchronous; allocates scratch with cudaMallocAsync. */
+int ecm_select(int64_t m, int32_t n_rows, const double *xf, double V0, int32_t m_target, const double *Omega,
+               int32_t k, int32_t power_its, int32_t *z, double *w, int32_t *n_sel, double *info, void *stream);
+
 /* Biot and Cauchy outputs for updated-Lagrangian macro codes (Sec. 3.2.2,
  * Eqs. workconjugacy and biotstress; Appendix A), from the homogenized
  * first Piola-Kirchhoff stress and its tangent at n points (Fbar = R U):

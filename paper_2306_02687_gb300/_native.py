@@ -48,6 +48,11 @@ SIGNATURES = {
                                       P(c_dbl), c_vp, c_vp, c_vp, c_vp, c_vp]),
     'rve_snapshots': (c_int, [c_int, c_vp, P(c_dbl), c_int, c_int, c_vp, c_int, c_dbl, c_dbl, c_int, c_int,
                               c_vp, c_vp, c_vp]),
+    'pod_modes': (c_int, [c_i64, c_int, c_vp, c_int, c_vp, c_int, c_vp, c_vp, c_vp, c_vp]),
+    'rve_mode_gradients': (c_int, [c_int, c_int, c_vp, c_vp, c_vp]),
+    'ecm_training_matrix': (c_int, [c_int, c_vp, P(c_dbl), c_int, c_vp, c_int, c_vp, c_vp, c_vp, c_vp]),
+    'ecm_select': (c_int, [c_i64, c_int, c_vp, c_dbl, c_int, c_vp, c_int, c_int, c_vp, c_vp, P(c_int), P(c_dbl),
+                           c_vp]),
     'rve_rom_biot_cauchy': (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'surrogate_linear_eval': (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'paths_kmeans': (c_int, [c_i64, c_int, c_vp, c_int, c_vp, c_vp, c_int, P(c_dbl), c_vp]),
