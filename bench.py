@@ -340,6 +340,8 @@ def main():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-adjoint', action='store_true', help='skip the timing of the implicit adjoint')
+    ap.add_argument('--no-other-workloads', action='store_true',
+                    help='skip the evaluation throughput of the other workloads (c1, c3, c4, c5)')
     ap.add_argument('--no-newton', action='store_true',
                     help='skip the timing of whole Newton iterations with the global macro solve')
     ap.add_argument('--no-oracle-check', action='store_true',
@@ -578,6 +580,11 @@ def main():
                "note": "rve_rom_adjoint (float64) at micro states converged by 12 float64 evaluations"}
         restore()
 
+    others = None
+    if not args.no_other_workloads and world == 1:
+        others = other_workloads(rv, [w for w in ('c1', 'c3', 'c4', 'c5') if w != args.workload],
+                                 args.precision, max(3, min(args.steps, 5)), dev, flush)
+
     newton = None
     if not args.no_newton:
         newton = newton_leg(rv, h, mesh, wl, u_host, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, types, R, Kv,
@@ -691,6 +698,7 @@ def main():
                   "note": "gradient, evaluation, assembly and norms captured in one CUDA graph"},
         "newton": newton,
         "adjoint": adj,
+        "other_workloads": others,
         "clocks": clocks,
         "other_form": {"precision": other, "value": world * n / (ms_other * 1e-3), "ms_per_step": ms_other},
         "speedup_vs_fp64_form": (ms_other / ms_step) if args.precision == 'mixed' else 1.0,
@@ -702,6 +710,58 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def other_workloads(rv, names, precision, steps, dev, flush):
+    """Throughput of the evaluation call on the other workloads (the
+    autotuner's kernels, the workload's macro field, micro states after
+    three mixed evaluations from a fresh state), for the record: evals/s
+    and ms per call, with the kernels used."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name in names:
+        wl = WORKLOADS[name]
+        paths = [os.path.join(ROOT, 'tests', 'golden', 'rom_%s.npz' % r) for r in wl['roms']]
+        if not all(os.path.exists(p) for p in paths):
+            continue
+        roms = [rv.load_rom_file(p) for p in paths]
+        h = rv.rve_rom_create(wl['d'], roms, roms[0]['V0'])
+        rv.rve_rom_autotune(h, precision, n_sample=16384)
+        X, conn = build_mesh(wl['mesh'])
+        mesh = rv.macro_mesh_create(X, conn)
+        n = mesh.n_ip
+        types = None
+        if len(roms) > 1:
+            types = torch.tensor(syn.type_labels(syn.SEED_BASE + 600, n, len(roms)), device=dev)
+        u = torch.tensor(macro_displacement(X, wl['load'], syn.SEED_BASE + 500), device=dev)
+        Fbar = torch.empty(n, wl['d'] ** 2, dtype=torch.float64, device=dev)
+        rv.macro_gradient(mesh, u, Fbar)
+        q, s, S, U = h.zero_state(n)
+        Pbar, dPdF, rnorm, status = h.outputs(n)
+        for _ in range(3):
+            rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=precision)
+        torch.cuda.synchronize()
+        st0 = [x.clone() for x in (q, s, S, U)]
+        tot = 0.0
+        for _ in range(steps):
+            for x, y in zip((q, s, S, U), st0):
+                x.copy_(y)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=precision)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / steps
+        out[name] = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms, "points": n,
+                     "failed_points": int((status != 0).sum().item()),
+                     "kernels": [rv.rve_rom_kernel_info(h, t, precision)[0] for t in range(len(roms))],
+                     "workload": wl['desc'], "state": "three mixed evaluations from a fresh state"}
+        h.destroy()
+        mesh.destroy()
+    return out
 
 
 def newton_leg(rv, h, mesh, wl, u_host, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, types, R, Kv, restore, args,

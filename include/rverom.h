@@ -224,6 +224,26 @@ int macro_gradient(rverom_mesh_t m, const double *u, double *Fbar, void *stream)
 int macro_assemble(rverom_mesh_t m, const double *Pbar, const double *dPdF, double *R,
                    double *Kvals, void *stream);
 
+/* The macro steps of one shard of a data-parallel monolithic iteration
+ * (Sec. 2: the element sums of Eq. 6 split over disjoint element ranges,
+ * the RVEs of a range evaluated where the range lives).
+ * macro_gradient_range: Fbar [(e_end - e_begin) * n_gp_per_elem][g] at the
+ * integration points of elements e_begin .. e_end - 1 (points numbered as
+ * in macro_gradient, the range's first point at Fbar[0]); u is the whole
+ * nodal field [n_nodes][d].
+ * macro_assemble_range: ADDS the range's element contributions to R
+ * [n_dof] and (when not NULL) Kvals [nnz] of the whole mesh's pattern;
+ * Pbar and dPdF hold the range's points only, in the order of
+ * macro_gradient_range.  Nothing is zeroed: the caller zeroes R and Kvals
+ * once, every range adds, and summing the shards' R and Kvals (an
+ * all-reduce across ranks) gives macro_assemble's result up to the order
+ * of the floating-point sums.  An empty range (e_end == e_begin) is a no-op.
+ * Errors: RVEROM_ERR_ARG for a range outside 0 .. n_elem or missing arrays. */
+int macro_gradient_range(rverom_mesh_t m, int64_t e_begin, int64_t e_end, const double *u,
+                         double *Fbar, void *stream);
+int macro_assemble_range(rverom_mesh_t m, int64_t e_begin, int64_t e_end, const double *Pbar,
+                         const double *dPdF, double *R, double *Kvals, void *stream);
+
 /* Convergence scalars of a monolithic iteration (device):
  *   out[0] = max |R| over DOFs with free_mask != 0
  *   out[1] = max |R| over DOFs with free_mask == 0 (reactions)
@@ -337,8 +357,12 @@ int ecm_training_matrix(int32_t n, const int32_t *phase, const double *moduli, i
 /* Empirical cubature (Sec. 3.3, Eq. SVDlambda and Box 1): the leading
  * m_target - 1 right singular vectors lambda of xf [n_rows][m] (device) by
  * randomized subspace iteration from the Gaussian test matrix Omega
- * [n_rows][k] (device, k >= m_target - 1; power_its power iterations,
- * Cholesky-QR re-orthonormalization), then the greedy selection of Box 1 on
+ * [n_rows][k] (device, m_target - 1 <= k <= n_rows; power_its power
+ * iterations; re-orthonormalization by SVQB, the Gram matrix's
+ * eigendecomposition, which drops directions of relative eigenvalue below
+ * 1e-15, so k may exceed the numerical rank of xf: k = n_rows with
+ * power_its = 0 spans the whole row space and gives the exact leading
+ * singular subspace), then the greedy selection of Box 1 on
  * J = [lambda 1]^T, b = [0 V0]^T: pick the available column most aligned
  * with r = b - J_z w (ties to the lowest index), least-squares weights,
  * non-negative least squares (Lawson-Hanson) when a weight is negative,

@@ -41,6 +41,8 @@ SIGNATURES = {
     'macro_mesh_csr': (c_int, [c_vp, P(c_i64), P(c_int)]),
     'macro_gradient': (c_int, [c_vp, c_vp, c_vp, c_vp]),
     'macro_assemble': (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    'macro_gradient_range': (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
+    'macro_assemble_range': (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'macro_residual_norms': (c_int, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     'macro_solve': (c_int, [c_vp, c_vp, c_vp, c_vp, c_dbl, c_int, c_vp, c_vp, c_vp, c_vp]),
     'rve_rom_mmax': (c_int, [c_vp, P(c_int)]),

@@ -259,6 +259,29 @@ def macro_assemble(m, Pbar, dPdF, R, Kvals=None, stream=None):
         _stream(stream)), 'macro_assemble')
 
 
+def macro_gradient_range(m, e_begin, e_end, u, Fbar, stream=None):
+    """Fbar at the integration points of elements e_begin .. e_end - 1 only
+    (one shard of a data-parallel macro problem)."""
+    n = (e_end - e_begin) * (m.n_ip // m.n_elem)
+    _native.check(_native.lib().macro_gradient_range(
+        m.ptr, e_begin, e_end, _ptr(u, torch.float64, (m.n_nodes, m.dim), 'u'),
+        _ptr(Fbar, torch.float64, (n, m.g), 'Fbar') if n > 0 else None,
+        _stream(stream)), 'macro_gradient_range')
+
+
+def macro_assemble_range(m, e_begin, e_end, Pbar, dPdF, R, Kvals=None, stream=None):
+    """Adds the contributions of elements e_begin .. e_end - 1 (their points'
+    Pbar and dPdF) to R and Kvals of the whole mesh; zeroes nothing."""
+    n = (e_end - e_begin) * (m.n_ip // m.n_elem)
+    _native.check(_native.lib().macro_assemble_range(
+        m.ptr, e_begin, e_end,
+        _ptr(Pbar, torch.float64, (n, m.g), 'Pbar') if n > 0 else None,
+        _ptr(dPdF, torch.float64, (n, m.g, m.g), 'dPdF') if (n > 0 and dPdF is not None) else None,
+        _ptr(R, torch.float64, (m.n_dof,), 'R'),
+        _ptr(Kvals, torch.float64, (m.nnz,), 'Kvals') if Kvals is not None else None,
+        _stream(stream)), 'macro_assemble_range')
+
+
 def macro_residual_norms(m, R, free_mask, rnorm, out, stream=None):
     n = rnorm.shape[0]
     _native.check(_native.lib().macro_residual_norms(

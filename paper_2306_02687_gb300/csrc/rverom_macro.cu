@@ -66,11 +66,12 @@ bool invert(int d, const double *J, double *Ji, double &det) {
     return true;
 }
 
-__global__ void k_gradient(int D, int nen, int ngp, int64_t n_ip, const int32_t *conn, const double *dN,
+__global__ void k_gradient(int D, int nen, int ngp, int64_t p0, int64_t n_ip, const int32_t *conn, const double *dN,
                            const double *u, double *Fbar) {
+    // points p0 .. p0 + n_ip - 1, written to Fbar from its start
     const int G = D * D;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_ip; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = p / ngp;
+    for (int64_t pl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pl < n_ip; pl += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = p0 + pl, e = p / ngp;
         double F[9];
         for (int c = 0; c < G; ++c) F[c] = (c % (D + 1) == 0) ? 1.0 : 0.0;
         for (int a = 0; a < nen; ++a) {
@@ -80,20 +81,21 @@ __global__ void k_gradient(int D, int nen, int ngp, int64_t n_ip, const int32_t 
                 for (int J = 0; J < D; ++J) F[i * D + J] += ui * dN[(p * nen + a) * D + J];
             }
         }
-        for (int c = 0; c < G; ++c) Fbar[p * G + c] = F[c];
+        for (int c = 0; c < G; ++c) Fbar[pl * G + c] = F[c];
     }
 }
 
 // one thread per (element, local row (a, i)): row of R_e and K_e, summed over
 // the element's integration points, scattered with atomics
 template <int D>
-__global__ void k_assemble(int64_t n_elem, const int32_t *conn, const double *dN, const double *wJ0,
+__global__ void k_assemble(int64_t e0, int64_t n_elem, const int32_t *conn, const double *dN, const double *wJ0,
                            const double *Pbar, const double *dPdF, const int32_t *kmap, double *R,
                            double *Kvals) {
+    // elements e0 .. e0 + n_elem - 1; Pbar and dPdF hold their points only
     constexpr int G = D * D, NEN = 1 << D, NGP = 1 << D, ND = NEN * D;
     const int64_t total = n_elem * ND;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = x / ND;
+        const int64_t el = x / ND, e = e0 + el;
         const int row = (int)(x % ND);
         const int a = row / D, i = row % D;
         double r = 0.0;
@@ -101,11 +103,11 @@ __global__ void k_assemble(int64_t n_elem, const int32_t *conn, const double *dN
 #pragma unroll
         for (int b = 0; b < ND; ++b) krow[b] = 0.0;
         for (int gp = 0; gp < NGP; ++gp) {
-            const int64_t p = e * NGP + gp;
+            const int64_t p = e * NGP + gp, pl = el * NGP + gp;
             const double w = wJ0[p];
             const double *dn = dN + p * NEN * D;
 #pragma unroll
-            for (int J = 0; J < D; ++J) r += w * Pbar[p * G + i * D + J] * dn[a * D + J];
+            for (int J = 0; J < D; ++J) r += w * Pbar[pl * G + i * D + J] * dn[a * D + J];
             if (Kvals) {
                 // t[kL] = w sum_J dN_a,J C[iJ][kL]
                 double t[G];
@@ -114,7 +116,7 @@ __global__ void k_assemble(int64_t n_elem, const int32_t *conn, const double *dN
 #pragma unroll
                 for (int J = 0; J < D; ++J) {
                     const double f = w * dn[a * D + J];
-                    const double *C = dPdF + (p * G + i * D + J) * G;
+                    const double *C = dPdF + (pl * G + i * D + J) * G;
 #pragma unroll
                     for (int c = 0; c < G; ++c) t[c] += f * C[c];
                 }
@@ -337,7 +339,31 @@ extern "C" int macro_mesh_csr(rverom_mesh_t m, int64_t *row_ptr, int32_t *col) {
 extern "C" int macro_gradient(rverom_mesh_t m, const double *u, double *Fbar, void *stream) {
     if (!m || !u || !Fbar) return RVEROM_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    k_gradient<<<grid_for(m->n_ip, m->n_sm), 256, 0, st>>>(m->dim, m->nen, m->ngp, m->n_ip, m->conn, m->dN, u, Fbar);
+    k_gradient<<<grid_for(m->n_ip, m->n_sm), 256, 0, st>>>(m->dim, m->nen, m->ngp, 0, m->n_ip, m->conn, m->dN, u,
+                                                           Fbar);
+    return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+}
+
+extern "C" int macro_gradient_range(rverom_mesh_t m, int64_t e_begin, int64_t e_end, const double *u, double *Fbar,
+                                    void *stream) {
+    if (!m || !u || (!Fbar && e_end > e_begin)) return RVEROM_ERR_ARG;
+    if (e_begin < 0 || e_end < e_begin || e_end > m->n_elem) return RVEROM_ERR_ARG;
+    if (e_end == e_begin) return RVEROM_OK;
+    const int64_t n = (e_end - e_begin) * m->ngp;
+    k_gradient<<<grid_for(n, m->n_sm), 256, 0, (cudaStream_t)stream>>>(m->dim, m->nen, m->ngp, e_begin * m->ngp, n,
+                                                                       m->conn, m->dN, u, Fbar);
+    return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+}
+
+static int launch_assemble(rverom_mesh_t m, int64_t e0, int64_t n_elem, const double *Pbar, const double *dPdF,
+                           double *R, double *Kvals, cudaStream_t st) {
+    const int64_t work = n_elem * m->nen * m->dim;
+    if (m->dim == 2)
+        k_assemble<2><<<grid_for(work, m->n_sm), 256, 0, st>>>(e0, n_elem, m->conn, m->dN, m->wJ0, Pbar, dPdF,
+                                                               m->kmap, R, Kvals);
+    else
+        k_assemble<3><<<grid_for(work, m->n_sm), 256, 0, st>>>(e0, n_elem, m->conn, m->dN, m->wJ0, Pbar, dPdF,
+                                                               m->kmap, R, Kvals);
     return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
 }
 
@@ -348,14 +374,16 @@ extern "C" int macro_assemble(rverom_mesh_t m, const double *Pbar, const double 
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), st) != cudaSuccess) return RVEROM_ERR_CUDA;
     if (Kvals && cudaMemsetAsync(Kvals, 0, m->nnz * sizeof(double), st) != cudaSuccess) return RVEROM_ERR_CUDA;
-    const int64_t work = m->n_elem * m->nen * m->dim;
-    if (m->dim == 2)
-        k_assemble<2><<<grid_for(work, m->n_sm), 256, 0, st>>>(m->n_elem, m->conn, m->dN, m->wJ0, Pbar, dPdF,
-                                                               m->kmap, R, Kvals);
-    else
-        k_assemble<3><<<grid_for(work, m->n_sm), 256, 0, st>>>(m->n_elem, m->conn, m->dN, m->wJ0, Pbar, dPdF,
-                                                               m->kmap, R, Kvals);
-    return cudaGetLastError() == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
+    return launch_assemble(m, 0, m->n_elem, Pbar, dPdF, R, Kvals, st);
+}
+
+extern "C" int macro_assemble_range(rverom_mesh_t m, int64_t e_begin, int64_t e_end, const double *Pbar,
+                                    const double *dPdF, double *R, double *Kvals, void *stream) {
+    if (!m || !R) return RVEROM_ERR_ARG;
+    if (e_begin < 0 || e_end < e_begin || e_end > m->n_elem) return RVEROM_ERR_ARG;
+    if (e_end == e_begin) return RVEROM_OK;
+    if (!Pbar || (Kvals && !dPdF)) return RVEROM_ERR_ARG;
+    return launch_assemble(m, e_begin, e_end - e_begin, Pbar, dPdF, R, Kvals, (cudaStream_t)stream);
 }
 
 extern "C" int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_mask, int64_t n_points,

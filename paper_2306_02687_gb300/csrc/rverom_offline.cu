@@ -693,43 +693,31 @@ void gemm(int M, int N, int K, const double *A, int64_t lda, const double *B, in
     k_gemm<TA, TB><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc);
 }
 
-// Cholesky of the k x k matrix G (lower factor in place, one CTA), with the
-// diagonal shifted by shift * trace / k; flag[0] = 1 on a non-positive pivot
-__global__ void __launch_bounds__(OT) k_cholesky(int k, double *G, double shift, int *flag) {
-    __shared__ double sh[OT / 32];
-    double tr = 0.0;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) tr += G[(int64_t)i * k + i];
-    tr = bsum(tr, sh);
-    for (int i = threadIdx.x; i < k; i += blockDim.x) G[(int64_t)i * k + i] += shift * tr / k;
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
+// SVQB orthonormalization (Stathopoulos and Wu, SIAM J. Sci. Comput. 23,
+// 2002) of the columns of M [m][k]: with the Gram matrix G = M^T M and the
+// column scaling D = diag(G)^-1/2, the eigendecomposition D G D = W Theta W^T
+// gives the orthonormal basis M D W Theta^-1/2 of span(M).  Directions with
+// Theta_j <= 1e-15 max Theta (numerically outside span(M), e.g. beyond the
+// rank of x_f) become zero columns instead of amplified rounding noise.
+// k_svqb_scale: dsc_j = G_jj^-1/2 (0 for a zero column), G <- D G D
+__global__ void __launch_bounds__(OT) k_svqb_scale(int k, double *G, double *dsc) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
         const double d = G[(int64_t)j * k + j];
-        if (!(d > 0.0)) {
-            if (threadIdx.x == 0) flag[0] = 1;
-            return;
-        }
-        const double l = sqrt(d);
-        __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(int64_t)i * k + j] /= l;
-        __syncthreads();
-        if (threadIdx.x == 0) G[(int64_t)j * k + j] = l;
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
-            const double lij = G[(int64_t)i * k + j];
-            for (int c = j + 1; c <= i; ++c) G[(int64_t)i * k + c] -= lij * G[(int64_t)c * k + j];
-        }
-        __syncthreads();
+        dsc[j] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
     }
+    __syncthreads();
+    for (int64_t x = threadIdx.x; x < (int64_t)k * k; x += blockDim.x) G[x] *= dsc[x / k] * dsc[x % k];
 }
 
-// Y <- Y L^-T row by row (Y [m][k], L lower: Y = Q L^T)
-__global__ void k_trsm_rows(int64_t m, int k, const double *L, double *Y) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
-        double *y = Y + r * k;
-        for (int j = 0; j < k; ++j) {
-            double v = y[j];
-            for (int i = 0; i < j; ++i) v -= y[i] * L[(int64_t)j * k + i];
-            y[j] = v / L[(int64_t)j * k + j];
-        }
+// C = D W Theta^-1/2 (k x k), Theta_j the diagonal that k_jacobi left in G,
+// theta_max = ev[0] (descending)
+__global__ void __launch_bounds__(OT) k_svqb_coef(int k, const double *G, const double *W, const double *ev,
+                                                  const double *dsc, double *C) {
+    const double tmax = ev[0];
+    for (int64_t x = threadIdx.x; x < (int64_t)k * k; x += blockDim.x) {
+        const int i = (int)(x / k), j = (int)(x % k);
+        const double th = G[(int64_t)j * k + j];
+        C[x] = (th > 1e-15 * tmax && tmax > 0.0) ? dsc[i] * W[x] / sqrt(th) : 0.0;
     }
 }
 
@@ -1036,8 +1024,8 @@ extern "C" int ecm_select(int64_t m, int32_t n_rows, const double *xf, double V0
     cudaStream_t st = (cudaStream_t)stream;
     const int L = m_target, cap = m_target + 1;
     double *Y = nullptr, *Z = nullptr, *G = nullptr, *V = nullptr, *ev = nullptr, *Lam = nullptr, *nrm = nullptr;
-    double *bv = nullptr, *scr = nullptr;
-    int *order = nullptr, *flag = nullptr, *bi = nullptr, *dz = nullptr, *dnz = nullptr, *act = nullptr;
+    double *bv = nullptr, *scr = nullptr, *T = nullptr, *C = nullptr, *dsc = nullptr;
+    int *order = nullptr, *bi = nullptr, *dz = nullptr, *dnz = nullptr, *act = nullptr;
     uint8_t *avail = nullptr;
     const int nb = 304;
     bool okm = cudaMallocAsync(&Y, (size_t)m * k * 8, st) == cudaSuccess &&
@@ -1046,7 +1034,9 @@ extern "C" int ecm_select(int64_t m, int32_t n_rows, const double *xf, double V0
                cudaMallocAsync(&V, (size_t)k * k * 8, st) == cudaSuccess &&
                cudaMallocAsync(&ev, (size_t)k * 8, st) == cudaSuccess &&
                cudaMallocAsync(&order, (size_t)k * 4, st) == cudaSuccess &&
-               cudaMallocAsync(&flag, 4, st) == cudaSuccess &&
+               cudaMallocAsync(&T, (size_t)m * k * 8, st) == cudaSuccess &&
+               cudaMallocAsync(&C, (size_t)k * k * 8, st) == cudaSuccess &&
+               cudaMallocAsync(&dsc, (size_t)k * 8, st) == cudaSuccess &&
                cudaMallocAsync(&Lam, (size_t)m * (L - 1) * 8, st) == cudaSuccess &&
                cudaMallocAsync(&nrm, (size_t)m * 8, st) == cudaSuccess &&
                cudaMallocAsync(&avail, (size_t)m, st) == cudaSuccess &&
@@ -1057,12 +1047,14 @@ extern "C" int ecm_select(int64_t m, int32_t n_rows, const double *xf, double V0
                cudaMallocAsync(&scr, ((size_t)L * cap * 2 + (size_t)cap * cap + 3 * (size_t)cap + L + 4 + cap) * 8, st) ==
                    cudaSuccess;
     int rc = okm ? RVEROM_OK : RVEROM_ERR_CUDA;
-    auto orth = [&](double *M) {  // M [m][k] <- orthonormal columns (Cholesky QR, twice)
+    auto orth = [&](double *M) {  // M [m][k] <- orthonormal basis of its span (SVQB, twice)
         for (int pass = 0; pass < 2; ++pass) {
             gemm<true, false>(k, k, (int)m, M, k, M, k, G, k, st);
-            cudaMemsetAsync(flag, 0, 4, st);
-            k_cholesky<<<1, OT, 0, st>>>(k, G, pass == 0 ? 1e-13 : 0.0, flag);
-            k_trsm_rows<<<(int)((m + 255) / 256), 256, 0, st>>>(m, k, G, M);
+            k_svqb_scale<<<1, OT, 0, st>>>(k, G, dsc);
+            k_jacobi<<<1, OT, 0, st>>>(k, G, V, order, ev, 60, nullptr);
+            k_svqb_coef<<<1, OT, 0, st>>>(k, G, V, ev, dsc, C);
+            gemm<false, false>((int)m, k, k, M, k, C, k, T, k, st);
+            cudaMemcpyAsync(M, T, (size_t)m * k * 8, cudaMemcpyDeviceToDevice, st);
         }
     };
     if (rc == RVEROM_OK) {
@@ -1127,7 +1119,7 @@ extern "C" int ecm_select(int64_t m, int32_t n_rows, const double *xf, double V0
         info[3] = 0.0;
     }
     for (void *ptr : {(void *)Y, (void *)Z, (void *)G, (void *)V, (void *)ev, (void *)Lam, (void *)nrm, (void *)bv,
-                      (void *)scr, (void *)order, (void *)flag, (void *)bi, (void *)dz, (void *)dnz, (void *)act,
+                      (void *)scr, (void *)T, (void *)C, (void *)dsc, (void *)order, (void *)bi, (void *)dz, (void *)dnz, (void *)act,
                       (void *)avail})
         if (ptr) cudaFreeAsync(ptr, st);
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == RVEROM_OK) rc = RVEROM_ERR_CUDA;

@@ -1,7 +1,8 @@
-"""Host-side multi-rank logic of the benchmark with two gloo ranks on CPU:
-the path shards macro points across ranks with no collective on the data
-path; only the step time is max-reduced and the throughput counts every
-rank's points (weak scaling)."""
+"""Host-side multi-rank logic with two gloo ranks on CPU.  The benchmark
+shards macro points across ranks with no collective on the data path; only
+the step time is max-reduced and the throughput counts every rank's points
+(weak scaling).  A monolithic Newton iteration shards the macro mesh by
+element range; the ranks' partial systems are summed by one all-reduce."""
 import os
 import socket
 
@@ -28,13 +29,69 @@ def _worker(rank, world, port, out):
 def test_weak_scaling_aggregate_two_gloo_ranks():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context('spawn').Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     # every rank sees the slowest rank's time; throughput = world * local points / max time
     assert out[0][0] == out[1][0] == 2.0
     assert out[0][1] == pytest.approx(world * 1000 / 2e-3)
     assert out[1][1] == pytest.approx(world * 2000 / 2e-3)
+
+
+def test_element_ranges_partition_the_mesh():
+    from paper_2306_02687_gb300.parallel import element_range
+    for n_elem in (0, 1, 5, 64, 1001):
+        for world in (1, 2, 3, 8):
+            rs = [element_range(n_elem, r, world) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == n_elem
+            assert all(rs[k][1] == rs[k + 1][0] for k in range(world - 1))
+            sizes = [b - a for a, b in rs]
+            assert min(sizes) >= 0 and max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        element_range(10, 2, 2)
+
+
+def _shard_worker(rank, world, port, out):
+    # every rank assembles its element range with the float64 oracle (the
+    # other ranges' points contribute nothing), the partial systems are
+    # summed through the package's all-reduce, and so are the norms
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from synthetic import meshes
+    from oracle import macro
+    from paper_2306_02687_gb300 import parallel
+    dist.init_process_group('gloo', init_method='tcp://127.0.0.1:%d' % port, rank=rank, world_size=world)
+    X, conn = meshes.rect(5, 3, 1.5, 1.0)
+    om = macro.MacroMesh(X, conn)
+    P = syn.perturbation(syn.SEED_BASE + 70, (om.n_ip, 2, 2), 0.1)
+    C = syn.perturbation(syn.SEED_BASE + 71, (om.n_ip, 4, 4), 1.0)
+    e0, e1 = parallel.element_range(om.n_el, rank, world)
+    keep = np.zeros(om.n_ip, dtype=bool)
+    keep[e0 * om.ngp:e1 * om.ngp] = True
+    R, K = om.assemble(np.where(keep[:, None, None], P, 0.0), np.where(keep[:, None, None], C, 0.0))
+    buf = torch.from_numpy(np.concatenate([R, K.toarray().ravel()]))
+    parallel.allreduce_system(buf)
+    norms = torch.tensor([1.0, 2.0, 0.5 + rank], dtype=torch.float64)
+    parallel.allreduce_norms(norms)
+    Rf, Kf = om.assemble(P, C)
+    full = np.concatenate([Rf, Kf.toarray().ravel()])
+    out[rank] = (float(np.abs(buf.numpy() - full).max() / np.abs(full).max()), norms.tolist(), e1 - e0)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_assembly_all_reduce_two_gloo_ranks():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context('spawn').Manager()
+    out = mgr.dict()
+    mp.spawn(_shard_worker, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        err, norms, n_el = out[r]
+        assert err <= 1e-14
+        assert norms == [1.0, 2.0, 1.5]
+        assert n_el == 8 if r == 0 else n_el == 7
 
 
 def test_reference_arm_other_ranks_exit_quietly():
