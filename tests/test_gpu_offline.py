@@ -86,7 +86,7 @@ def test_offline_pipeline_matches_oracle():
     # 30 x 30 least-squares system; whole row space: rounding of the Gram
     # eigenproblem, ~1e-12, amplified the same way)
     n_rows = xf_or.shape[0]
-    xo = torch.tensor(xf_or, device='cuda')
+    xo = torch.tensor(np.ascontiguousarray(xf_or), device='cuda').contiguous()
     for k, its, wtol in ((m_target - 1 + 10, 2, 1e-4), (n_rows, 0, 1e-6)):
         Om = torch.tensor(syn.rng(syn.SEED_BASE + 323).standard_normal((n_rows, k)), device='cuda')
         ze, we, ie = offline.ecm_select(xo, 1.0, m_target, Om, power_its=its)
