@@ -129,7 +129,10 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
     const int64_t off = (a.perm && a.offset) ? (int64_t)(*a.offset) : 0;
     const int32_t *perm = a.perm ? a.perm + off : nullptr;
     float *ws = a.cond + off * CR::W;  // records of this type's points, by list position
-    const int64_t n_tiles = (count + NP - 1) / NP;
+    // this CTA's share of the list: a contiguous range (shares differ by at
+    // most one point), taken in tiles of NP points with a partial last tile
+    // whose missing points cost (almost) nothing
+    const int64_t r_begin = count * blockIdx.x / gridDim.x, r_end = count * (blockIdx.x + 1) / gridDim.x;
     const int nch = (m + CI - 1) / CI;
     // this warp's tile: points p0 .. p0 + PPT - 1 of the CTA, its A rows, its
     // TMEM accumulator columns, its MMA commit barriers
@@ -156,8 +159,12 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         tc::mbar_init_fence();
         *s_err = 0;
     }
-    // staging buffers: zero once (entries past m keep finite values)
+    // staging buffers: zero once (entries past m keep finite values); the
+    // A-operand buffers too (a warp without points in a tile leaves them as
+    // they are, and its MMAs read them)
     for (int x = tid; x < 2 * NBST; x += NT) s_Bst[x] = make_float2(0.0f, 0.0f);
+    for (int x = tid; x < (int)(NW * PL::YWARP / 4); x += NT) reinterpret_cast<float *>(smem + PL::o_Y)[x] = 0.0f;
+    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -201,13 +208,15 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                      &s_bar[buf]);
     };
 
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int64_t t0 = r_begin; t0 < r_end; t0 += NP) {
+        const int nlive = (int)min((int64_t)NP, r_end - t0);  // points of this tile
+        const bool wlive = p0 < nlive;                         // this warp's tile holds points
         // ---- a1: polar split, micro update ---------------------------------
         if (tid < NP) {
             const int p = tid;
-            const int64_t li = tile * NP + p;
+            const int64_t li = t0 + p;
             int gp = -1;
-            if (li < count) gp = perm ? perm[li] : (int)li;
+            if (p < nlive) gp = perm ? perm[li] : (int)li;
             s_pidx[p] = gp;
             int flag = -1;
             double F[G], R[G], U[G];
@@ -355,6 +364,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 float *Yh = yw + yb * 2048, *Yl = Yh + 1024;
 #pragma unroll
                 for (int e = 0; e < EPS; ++e) {
+                    if (!wlive) break;
                     const int il = ks * EPS + e;
                     float bx[G];
 #pragma unroll
@@ -411,14 +421,16 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             // all of this lane's rows at once (2 RPW independent chains); a row
             // past the warp's points reads row 0 and is never stored, and rows
             // j >= n are stored as zero
-            {
+            if (wlive) {
                 int bo[RPW], wo[RPW];
+                bool lv[RPW];  // the row belongs to a point of the tile
 #pragma unroll
                 for (int u = 0; u < RPW; ++u) {
                     const int o = lane + 32 * u;
                     const bool in = o < PPT * NQ;
                     wo[u] = in ? o / NQ : 0;
                     bo[u] = in ? o % NQ : 0;
+                    lv[u] = in && p0 + o / NQ < nlive;
                 }
 #pragma unroll
                 for (int il = 0; il < CI; il += 2)
@@ -426,6 +438,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     for (int c = 0; c < G; ++c)
 #pragma unroll
                         for (int u = 0; u < RPW; ++u) {
+                            if (!lv[u]) continue;
                             const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * PPT + wo[u];
                             const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
                             const float2 x0 = B2[b0], y0 = WP2[w0], x1 = B2[b1], y1 = WP2[w1];
@@ -460,6 +473,7 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                 const int qd = warp & 3;
                 const uint32_t lanes = (uint32_t)(qd * 32) << 16;
                 for (int t = warp >> 2; t < NW; t += 2) {
+                    if (t * PPT >= nlive) break;  // tiles without points (their rows are never read)
                     const int row = t * 128 + qd * 32 + lane;
                     const int p = row / NAR, jr = row % NAR;
 #pragma unroll
@@ -479,9 +493,9 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                         }
                         if (!last) {
                             tc::tmem_st32(tbase + lanes + NW * NN + t * NN + cb * 32, va);
-                        } else if (jr < NA && tile * NP + p < count) {
+                        } else if (jr < NA && p < nlive) {
                             // lane jr holds column jr of M: entries (col, jr), col >= jr
-                            float *rm = ws + (tile * NP + p) * CR::W + CR::o_M;
+                            float *rm = ws + (t0 + p) * CR::W + CR::o_M;
 #pragma unroll
                             for (int c = 0; c < 32; ++c) {
                                 const int col = cb * 32 + c;
@@ -506,8 +520,8 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                         }
                         if (!last) {
                             tc::tmem_st16(tbase + lanes + NW * NN + t * NN + cb * 32, va);
-                        } else if (jr < NA && tile * NP + p < count) {
-                            float *rm = ws + (tile * NP + p) * CR::W + CR::o_M;
+                        } else if (jr < NA && p < nlive) {
+                            float *rm = ws + (t0 + p) * CR::W + CR::o_M;
 #pragma unroll
                             for (int c = 0; c < 16; ++c) {
                                 const int col = cb * 32 + c;
@@ -533,8 +547,8 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             const int o = lane + 32 * u;
             if (o < PPT * NQ) {
                 const int pl = o / NQ, jj = o % NQ;
-                const int64_t li = tile * NP + p0 + pl;
-                if (li < count) {
+                const int64_t li = t0 + p0 + pl;
+                if (p0 + pl < nlive) {
                     const df v = jj < n ? df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1])) : df{0.0f, 0.0f};
                     float *rec = ws + li * CR::W;
                     rec[CR::o_rh + jj] = v.hi;
@@ -545,8 +559,8 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
         }
         if (lane < PPT * G) {
             const int pl = lane / G, c = lane % G;
-            const int64_t li = tile * NP + p0 + pl;
-            if (li < count) {
+            const int64_t li = t0 + p0 + pl;
+            if (p0 + pl < nlive) {
                 float *rec = ws + li * CR::W;
                 rec[CR::o_ph + c] = pudf.hi;
                 rec[CR::o_pl + c] = pudf.lo;

@@ -135,7 +135,10 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
     const int64_t off = (a.perm && a.offset) ? (int64_t)(*a.offset) : 0;
     const int32_t *perm = a.perm ? a.perm + off : nullptr;
     float *ws = a.cond + off * CR::W;  // records of this type's points, by list position
-    const int64_t n_tiles = (count + NP - 1) / NP;
+    // this CTA's share of the list: a contiguous range (shares differ by at
+    // most one point), taken in tiles of NP points with a partial last tile
+    // whose missing points cost (almost) nothing
+    const int64_t r_begin = count * blockIdx.x / gridDim.x, r_end = count * (blockIdx.x + 1) / gridDim.x;
     const int nch = (m + CI - 1) / CI;
 
     if (warp == 0) {
@@ -155,8 +158,12 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
         tc::mbar_init_fence();
         *s_err = 0;
     }
-    // staging buffers: zero once (entries past m keep finite values)
+    // staging buffers: zero once (entries past m keep finite values); the
+    // A-operand buffers too (a warp without points in a tile leaves them as
+    // they are, and its MMAs read them)
     for (int x = tid; x < 2 * NBST; x += NT) s_Bst[x] = make_float2(0.0f, 0.0f);
+    for (int x = tid; x < (int)(NW * PL::YWARP / 4); x += NT) reinterpret_cast<float *>(smem + PL::o_Y)[x] = 0.0f;
+    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -204,7 +211,8 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
         tc::regs_dec<PL::REGS_HELP>();
         const uint32_t tbase = tbase_init;
         uint32_t gc = 0, gstep = 0;  // chunks and k-steps of this CTA before the current tile
-        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int64_t t0 = r_begin; t0 < r_end; t0 += NP) {
+            const int nlive = (int)min((int64_t)NP, r_end - t0);  // points of this tile
             // tables of the first two chunks (the buffers are free since barrier C)
             stage(gc, 0);
             if (nch > 1) stage(gc + 1, 1);
@@ -215,11 +223,13 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
             const uint32_t lanes = (uint32_t)(qd * 32) << 16;
             // residual rows o = ht + NHT u: point o / NQ, mode o % NQ
             int bo[RPH], wo[RPH];
+            bool lv[RPH];  // the row belongs to a point of the tile
 #pragma unroll
             for (int u = 0; u < RPH; ++u) {
                 const int o = ht + NHT * u;
                 const bool in = o < NP * NQ;
                 const int p = in ? o / NQ : 0;
+                lv[u] = in && p < nlive;
                 bo[u] = in ? o % NQ : 0;
                 wo[u] = (p / PPT) * CI * G * PPT + p % PPT;  // w P of point p: [warp][il][c][pl]
             }
@@ -248,6 +258,7 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                     tc::fence_after_sync();
                     const bool kahan = ch > 0;
                     for (int t = 0; t < NW; ++t) {
+                        if (t * PPT >= nlive) break;  // tiles without points (their rows are never read)
                         const int row = t * 128 + qd * 32 + lane;
                         const int p = row / NAR, jr = row % NAR;
 #pragma unroll
@@ -268,9 +279,9 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                             }
                             if (!last) {
                                 tc::tmem_st16(ca + NW * NN, va);
-                            } else if (jr < NA && tile * NP + p < count) {
+                            } else if (jr < NA && p < nlive) {
                                 // lane jr holds column jr of M: entries (col, jr), col >= jr
-                                float *rm = ws + (tile * NP + p) * CR::W + CR::o_M;
+                                float *rm = ws + (t0 + p) * CR::W + CR::o_M;
 #pragma unroll
                                 for (int c = 0; c < 16; ++c) {
                                     const int col = cb * 16 + c;
@@ -296,13 +307,14 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                         for (int c = 0; c < G; ++c)
 #pragma unroll
                             for (int u = 0; u < RPH; ++u) {
+                                if (!lv[u]) continue;
                                 const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * PPT + wo[u];
                                 const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
                                 const float2 x0 = B2[b0], y0 = WP[w0], x1 = B2[b1], y1 = WP[w1];
                                 dacc_fma(rdacc[2 * u], x0.x, x0.y, y0.x, y0.y);
                                 dacc_fma(rdacc[2 * u + 1], x1.x, x1.y, y1.x, y1.y);
                             }
-                    if (ht < NP * G) {
+                    if (ht < NP * G && pp < nlive) {
                         for (int il = 0; il < CI; ++il) {
                             const float2 v = WP[(il * G + pc) * PPT + pwo];
                             pudf = df_add(pudf, df{v.x, v.y});
@@ -327,8 +339,8 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                 const int o = ht + NHT * u;
                 if (o < NP * NQ) {
                     const int p = o / NQ, jj = o % NQ;
-                    const int64_t li = tile * NP + p;
-                    if (li < count) {
+                    const int64_t li = t0 + p;
+                    if (p < nlive) {
                         const df v = jj < n ? df_add(dacc_get(rdacc[2 * u]), dacc_get(rdacc[2 * u + 1])) : df{0.0f, 0.0f};
                         float *rec = ws + li * CR::W;
                         rec[CR::o_rh + jj] = v.hi;
@@ -338,8 +350,8 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                 }
             }
             if (ht < NP * G) {
-                const int64_t li = tile * NP + pp;
-                if (li < count) {
+                const int64_t li = t0 + pp;
+                if (pp < nlive) {
                     float *rec = ws + li * CR::W;
                     rec[CR::o_ph + pc] = pudf.hi;
                     rec[CR::o_pl + pc] = pudf.lo;
@@ -364,13 +376,14 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
         constexpr int NTT = 32 * NW;
         const uint32_t tbase = tbase_init;
         uint32_t gc = 0, gstep = 0;
-        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int64_t t0 = r_begin; t0 < r_end; t0 += NP) {
+            const int nlive = (int)min((int64_t)NP, r_end - t0);  // points of this tile
             // ---- a1: polar split, micro update ------------------------------
             if (tid < NP) {
                 const int p = tid;
-                const int64_t li = tile * NP + p;
+                const int64_t li = t0 + p;
                 int gp = -1;
-                if (li < count) gp = perm ? perm[li] : (int)li;
+                if (p < nlive) gp = perm ? perm[li] : (int)li;
                 s_pidx[p] = gp;
                 int flag = -1;
                 double F[G], R[G], U[G];
@@ -425,6 +438,7 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
             }
             tc::named_bar(0, NT);  // A
             const int p0 = warp * PPT;
+            const bool wlive = p0 < nlive;  // this warp's tile holds points
             float *yw = reinterpret_cast<float *>(smem + PL::o_Y + warp * PL::YWARP);
             float *Ww = s_W + warp * CI * PPT * G * G;
             uint64_t *mbar = b_commit + 2 * warp;
@@ -518,6 +532,7 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                     float *Yh = yw + yb * 2048, *Yl = Yh + 1024;
 #pragma unroll
                     for (int e = 0; e < EPS; ++e) {
+                        if (!wlive) break;
                         const int il = ks * EPS + e;
                         float bx[G];
 #pragma unroll

@@ -263,7 +263,9 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
 
 @pytest.mark.parametrize('seed', range(40))
 def test_protocol_is_hazard_free(seed):
-    assert not run_schedule(seed, n_tiles=1 + seed % 3, nch=1 + (seed // 3) % 6)
+    # a CTA's contiguous share of the points may hold no tile at all (fewer
+    # points than CTAs): n_tiles = 0 only drains
+    assert not run_schedule(seed, n_tiles=seed % 4, nch=1 + (seed // 3) % 6)
 
 
 @pytest.mark.parametrize('seed', range(30))
@@ -409,7 +411,7 @@ def run_single_role(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, ti
 
 @pytest.mark.parametrize('seed', range(20))
 def test_single_role_protocol_is_hazard_free(seed):
-    run_single_role(seed, n_tiles=1 + seed % 2, nch=1 + seed % 5)
+    run_single_role(seed, n_tiles=seed % 3, nch=1 + seed % 5)
 
 
 @pytest.mark.parametrize('seed', range(20))
