@@ -423,14 +423,12 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
             // j >= n are stored as zero
             if (wlive) {
                 int bo[RPW], wo[RPW];
-                bool lv[RPW];  // the row belongs to a point of the tile
 #pragma unroll
                 for (int u = 0; u < RPW; ++u) {
                     const int o = lane + 32 * u;
                     const bool in = o < PPT * NQ;
                     wo[u] = in ? o / NQ : 0;
                     bo[u] = in ? o % NQ : 0;
-                    lv[u] = in && p0 + o / NQ < nlive;
                 }
 #pragma unroll
                 for (int il = 0; il < CI; il += 2)
@@ -438,7 +436,6 @@ __global__ void __launch_bounds__(256, 1) eval_tc_kernel(EvalArgs a) {
                     for (int c = 0; c < G; ++c)
 #pragma unroll
                         for (int u = 0; u < RPW; ++u) {
-                            if (!lv[u]) continue;
                             const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * PPT + wo[u];
                             const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
                             const float2 x0 = B2[b0], y0 = WP2[w0], x1 = B2[b1], y1 = WP2[w1];

@@ -223,13 +223,11 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
             const uint32_t lanes = (uint32_t)(qd * 32) << 16;
             // residual rows o = ht + NHT u: point o / NQ, mode o % NQ
             int bo[RPH], wo[RPH];
-            bool lv[RPH];  // the row belongs to a point of the tile
 #pragma unroll
             for (int u = 0; u < RPH; ++u) {
                 const int o = ht + NHT * u;
                 const bool in = o < NP * NQ;
                 const int p = in ? o / NQ : 0;
-                lv[u] = in && p < nlive;
                 bo[u] = in ? o % NQ : 0;
                 wo[u] = (p / PPT) * CI * G * PPT + p % PPT;  // w P of point p: [warp][il][c][pl]
             }
@@ -307,7 +305,6 @@ __global__ void __launch_bounds__(384, 1) eval_tc_ws_kernel(EvalArgs a) {
                         for (int c = 0; c < G; ++c)
 #pragma unroll
                             for (int u = 0; u < RPH; ++u) {
-                                if (!lv[u]) continue;
                                 const int b0 = (il * G + c) * BP + bo[u], w0 = (il * G + c) * PPT + wo[u];
                                 const int b1 = b0 + G * BP, w1 = w0 + G * PPT;
                                 const float2 x0 = B2[b0], y0 = WP[w0], x1 = B2[b1], y1 = WP[w1];
