@@ -56,6 +56,7 @@ bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) |
 #define RV_SYM(D, NA, TA, NP, CI, KT) &launch_cfg<D, NA, TA, TA, NP, CI, KT, false, true>
 #define RV_TC(D, NA, NP, CI) &launch_tc<D, NA, NP, CI>
 #define RV_TCWS(D, NA, NP, CI) &launch_tc_ws<D, NA, NP, CI>
+#define RV_TCW(D, NA, CI, FK) &launch_tc_wide<D, NA, CI, FK>
 
 int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, CandInfo *info) {
     LaunchFn c[4] = {};
@@ -88,9 +89,11 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, C
             add(RV_SYM(2, 36, 6, 12, 16, float), "simt-symmetric <2,36> 6x6 blocks, 12 points x 16 ECM", 1);
             add(RV_SYM(2, 36, 6, 12, 8, float), "simt-symmetric <2,36> 6x6 blocks, 12 points x 8 ECM", 1);
             add(RV_FUSED(2, 36, 9, 9, 16, 8, float), "simt-fused <2,36> 16 points x 8 ECM", 1);
+            add(RV_TCW(2, 36, 8, 4), "tcgen05-tf32x3 wide <2,36> 5 tile + 4 helper warps, 20 points x 8 ECM, fold per 4 k-steps", 2);
         } else if (n <= 64) {
             add(RV_SYM(2, 72, 6, 3, 16, float), "simt-symmetric <2,72> 6x6 blocks, 3 points x 16 ECM", 1);
             add(RV_FUSED(2, 72, 9, 9, 4, 8, float), "simt-fused <2,72> 4 points x 8 ECM", 1);
+            add(RV_TCW(2, 68, 16, 2), "tcgen05-tf32x3 wide <2,68> 3 tile + 4 helper warps, 6 points x 16 ECM, fold per 2 k-steps", 2);
         }
     } else if (dim == 2) {
         if (n <= 12) add(RV_FUSED(2, 16, 4, 4, 16, 8, double), "fp64-fused <2,16> 16 points x 8 ECM", 1);
@@ -123,6 +126,20 @@ int tc_record_words(int dim, int n) {
     if (n <= 12) return CondRec<2, 16>::W;
     if (n <= 16) return 0;
     if (n <= 24) return CondRec<2, 28>::W;
+    if (n <= 32) return CondRec<2, 36>::W;
+    if (n <= 64) return CondRec<2, 68>::W;
+    return 0;
+}
+
+// columns N of the B-operand image: those of the tensor-core kernel serving
+// n modes (its augmented size NA rounded up to 16)
+int tc_image_nn(int dim, int n) {
+    if (dim != 2) return 0;
+    if (n <= 12) return 16;
+    if (n <= 16) return 0;
+    if (n <= 24) return 32;
+    if (n <= 32) return 48;
+    if (n <= 64) return 80;
     return 0;
 }
 
@@ -231,7 +248,7 @@ extern "C" int rve_rom_create(int32_t dim, int32_t n_types, const rverom_type_de
         td.Bimg = nullptr;
         td.img_nn = 0;
         if (ok && tc_record_words(dim, d.n_modes) > 0) {  // a tensor-core candidate serves this type
-            const int nn = (d.n_modes + g + 15) / 16 * 16;
+            const int nn = tc_image_nn(dim, d.n_modes);
             std::vector<float> img = tc_table_image(d, g, nn);
             float *bi = nullptr;
             ok = cudaMalloc(&bi, img.size() * sizeof(float)) == cudaSuccess &&

@@ -8,6 +8,7 @@
 #include "rom_ws.cuh"
 #include "rom_tc.cuh"
 #include "rom_tc_ws.cuh"
+#include "rom_tc_wide.cuh"
 
 struct rverom_s {
     int dim = 2;
@@ -137,7 +138,40 @@ cudaError_t launch_tc_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaSt
     ckern<<<(unsigned)cgrid, CT * TPP, CP::bytes, st>>>(a);
     return cudaGetLastError();
 }
+// tensor-core kernel for wide planar ROMs (NA = 36 or 68) and the
+// condensation kernel (CT points per CTA, so that its shared-memory copy of
+// the augmented systems fits)
+template <int D, int NA, int CI, int FK>
+cudaError_t launch_tc_wide(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
+    using PL = TcWidePlan<D, NA, CI, FK>;
+    constexpr int CT = NA <= 36 ? 32 : 16, TPP = 256 / CT;
+    using CP = CondPlan<D, NA, CT, TPP>;
+    static_assert(CP::bytes <= 227 * 1024, "condensation shared memory");
+    if (!a.t.Bimg || a.t.img_nn != PL::NN || !a.cond) return cudaErrorInvalidValue;
+    auto kern = eval_tc_wide_kernel<D, NA, CI, FK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes);
+    if (e != cudaSuccess) return e;
+    auto ckern = condense_kernel<D, NA, CT, TPP>;
+    e = cudaFuncSetAttribute(ckern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP::bytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ckern, CT * TPP, CP::bytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int64_t tiles = (max_points + PL::NP - 1) / PL::NP;
+    int64_t grid = n_sm;
+    if (tiles < grid) grid = tiles;
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = (int)grid;
+    kern<<<(unsigned)grid, PL::NT, PL::bytes, st>>>(a);
+    int64_t cgrid = (max_points + CT - 1) / CT, cmax = (int64_t)n_sm * occ;
+    if (cgrid > cmax) cgrid = cmax;
+    if (cgrid < 1) cgrid = 1;
+    ckern<<<(unsigned)cgrid, CT * TPP, CP::bytes, st>>>(a);
+    return cudaGetLastError();
+}
 int tc_record_words(int dim, int n);
+int tc_image_nn(int dim, int n);
 
 // Tile configuration of the adjoint (float64 form) per (dimension, n~ bucket).
 inline cudaError_t dispatch_adjoint(int dim, int n, const EvalArgs &a, int n_sm, int64_t max_points,

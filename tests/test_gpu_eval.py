@@ -349,7 +349,8 @@ def tensor_core_candidates(h, t=0):
     return [(c, nm) for c, nm in enumerate(names) if nm.startswith('tcgen05')]
 
 
-@pytest.mark.parametrize('name,kind', [('c1', 'single-role'), ('c2', 'single-role'), ('c2', 'warp-specialized')])
+@pytest.mark.parametrize('name,kind', [('c1', 'single-role'), ('c2', 'single-role'), ('c2', 'warp-specialized'),
+                                       ('c5b', 'wide'), ('c5c', 'wide')])
 def test_tensor_core_kernel_many_tiles(name, kind):
     # each tcgen05 candidate, selected by name, in the launch configuration of
     # the benchmark: a persistent grid of one CTA per SM working through at
@@ -363,7 +364,10 @@ def test_tensor_core_kernel_many_tiles(name, kind):
         pytest.skip('ROM file not generated')
     h, oroms = _handle([name])
     orom = oroms[0]
-    cands = [(c, nm) for c, nm in tensor_core_candidates(h) if ('helper' in nm) == (kind == 'warp-specialized')]
+    pick = {'single-role': lambda nm: 'helper' not in nm,
+            'warp-specialized': lambda nm: 'helper' in nm and 'wide' not in nm,
+            'wide': lambda nm: 'wide' in nm}[kind]
+    cands = [(c, nm) for c, nm in tensor_core_candidates(h) if pick(nm)]
     assert len(cands) == 1, cands
     cand, cname = cands[0]
     n_pts_cta = int(re.search(r'(\d+) points', cname).group(1))
@@ -409,7 +413,7 @@ def test_tensor_core_kernel_many_tiles(name, kind):
         assert np.array_equal(g2[k], g[k]), k
 
 
-@pytest.mark.parametrize('name,n_keep', [('c1', 10), ('c2', 20), ('c2', 17)])
+@pytest.mark.parametrize('name,n_keep', [('c1', 10), ('c2', 20), ('c2', 17), ('c5b', 28), ('c5c', 40)])
 def test_truncated_rom_every_candidate(name, n_keep):
     # a ROM with fewer modes than its tile configuration holds (padding rows
     # and columns of the augmented system, and of the tensor-core A operand

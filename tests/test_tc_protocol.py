@@ -62,24 +62,30 @@ class Hazard(AssertionError):
 
 
 def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeout_at=None, drain=True,
-                 latency=30, clock=False):
+                 latency=30, clock=False, nw=NW, ksc=KSC, fk=None):
     """timeout_at: the first wait still blocked at or after this model time
-    runs out.  Returns True when a timeout was injected; raises Hazard."""
+    runs out.  Returns True when a timeout was injected; raises Hazard.
+    nw tile warps, ksc k-steps per chunk, a fold every fk k-steps (default:
+    once per chunk, the warp-specialized kernel; the wide kernel folds every
+    2 or 4 k-steps with 3 or 5 tile warps)."""
+    fk = ksc if fk is None else fk
+    ngr = ksc // fk
     rng = random.Random(seed)
     err = [False]                        # the CTA's timeout flag
-    inflight = {'mma': [0] * NW, 'copy': 0}
+    inflight = {'mma': [0] * nw, 'copy': 0}
     bx = [Barrier(1), Barrier(1)]
-    commit = [[Barrier(1), Barrier(1)] for _ in range(NW)]
-    chunk = [Barrier(1) for _ in range(NW)]
+    commit = [[Barrier(1), Barrier(1)] for _ in range(nw)]
+    chunk = [Barrier(1) for _ in range(nw)]
     staged = [Barrier(NH), Barrier(NH)]   # one arrival per helper warp's copies
-    wp = [Barrier(NW), Barrier(NW)]
+    wp = [Barrier(nw), Barrier(nw)]
     res = [Barrier(NH), Barrier(NH)]
     fold = Barrier(NH)
-    named = {0: NamedBarrier(NW + NH), 1: NamedBarrier(NH), 2: NamedBarrier(NW)}
+    named = {0: NamedBarrier(nw + NH), 1: NamedBarrier(NH), 2: NamedBarrier(nw)}
     events = []        # (time, action) of the asynchronous engines
     last_mma = {}      # per warp: completion time of its latest MMA group
     now = [0]
-    mma_done, mma_issued, folded = set(), set(), {}
+    mma_done, mma_issued, folded = set(), set(), {}   # per (warp, fold group)
+    chunk_done = set()                                 # per (warp, chunk)
     wp_written, res_done, landed, readers, y_busy = {}, {}, set(), {}, {}
 
     def check(cond, what):
@@ -122,7 +128,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
         b = g & 1
         check(readers.get(g - 2, 0) == 0, 'tables of chunk %d overwritten while read' % (g - 2))
         if g >= 2:
-            check(all((w, g - 2) in mma_done for w in range(NW)), 'B image of chunk %d overwritten' % (g - 2))
+            check(all((w, g - 2) in chunk_done for w in range(nw)), 'B image of chunk %d overwritten' % (g - 2))
 
         def land():
             inflight['copy'] -= 1
@@ -138,7 +144,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
         later(land_bx)
 
     def helper(h):
-        gc = gs = 0
+        gc = gs = gg = 0
         for _ in range(n_tiles):
             if h == 0:
                 stage(gc)
@@ -148,24 +154,26 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
             for ch in range(nch):
                 g = gc + ch
                 b = g & 1
-                sl = gs + ch * KSC + KSC - 1
-                for w in range(NW):
-                    if fold_wait == 'chunk':
-                        yield from wait(chunk[w], g & 1)
-                    elif fold_wait == 'buffer':
-                        yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
-                    else:  # both phases of the buffer barrier in turn
-                        yield from wait(commit[w][sl & 1], ((sl >> 1) & 1) ^ 1)
-                        yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
-                for w in range(NW):
-                    check((w, g) in mma_done, 'fold of chunk %d before its MMAs completed' % g)
-                    check((w, g + 1) not in mma_issued, 'fold of chunk %d while chunk %d runs' % (g, g + 1))
-                    folded.setdefault((w, g), set()).add(h)
-                    yield
-                fold.arrive()
+                for gi in range(ngr):
+                    gr = gg + ch * ngr + gi
+                    sl = gs + ch * ksc + gi * fk + fk - 1       # the group's last k-step
+                    for w in range(nw):
+                        if fold_wait == 'chunk':
+                            yield from wait(chunk[w], gr & 1)
+                        elif fold_wait == 'buffer':
+                            yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+                        else:  # both phases of the buffer barrier in turn
+                            yield from wait(commit[w][sl & 1], ((sl >> 1) & 1) ^ 1)
+                            yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+                    for w in range(nw):
+                        check((w, gr) in mma_done, 'fold of group %d before its MMAs completed' % gr)
+                        check((w, gr + 1) not in mma_issued, 'fold of group %d while group %d runs' % (gr, gr + 1))
+                        folded.setdefault((w, gr), set()).add(h)
+                        yield
+                    fold.arrive()
                 yield from wait(wp[b], (g >> 1) & 1)
                 yield from wait(staged[b], (g >> 1) & 1)
-                check(len(wp_written.get(g, ())) == NW, 'residual of chunk %d before w P' % g)
+                check(len(wp_written.get(g, ())) == nw, 'residual of chunk %d before w P' % g)
                 check(g in landed, 'residual of chunk %d before its tables' % g)
                 readers[g] = readers.get(g, 0) + 1
                 yield
@@ -178,7 +186,8 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                         stage(g + 2)
             yield from sync(0)
             gc += nch
-            gs += nch * KSC
+            gs += nch * ksc
+            gg += nch * ngr
             yield from sync(0)
         if drain and h == 0:
             yield from drain_wait(lambda: inflight['copy'] == 0)
@@ -191,7 +200,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
             raise Hazard('TMEM freed or CTA ended with MMAs or copies in flight')
 
     def tile(w):
-        gc = gs = 0
+        gc = gs = gg = 0
         for _ in range(n_tiles):
             yield from sync(2)
             yield from sync(0)
@@ -206,8 +215,9 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                 readers[g] = readers.get(g, 0) + 1
                 wp_written.setdefault(g, set()).add(w)
                 wp[b].arrive()
-                for ks in range(KSC):
-                    s = gs + ch * KSC + ks
+                for ks in range(ksc):
+                    s = gs + ch * ksc + ks
+                    gr = gg + ch * ngr + ks // fk
                     yb = s & 1
                     if s >= 2:
                         yield from wait(commit[w][yb], ((s - 2) >> 1) & 1)
@@ -215,34 +225,38 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                     yield
                     if ks == 0:
                         yield from wait(bx[b], (g >> 1) & 1)
-                        if g >= 1:
-                            yield from wait(fold, (g - 1) & 1)
-                            check(len(folded.get((w, g - 1), ())) == NH, 'MMAs of chunk %d before the fold' % g)
+                    if ks % fk == 0 and gr >= 1:
+                        yield from wait(fold, (gr - 1) & 1)
+                        check(len(folded.get((w, gr - 1), ())) == NH, 'MMAs of group %d before the fold' % gr)
                     if err[0]:                   # no MMA is issued after a timeout
                         continue
-                    mma_issued.add((w, g))
+                    mma_issued.add((w, gr))
                     y_busy[(w, yb)] = y_busy.get((w, yb), 0) + 1
-                    last = ks == KSC - 1
+                    glast = ks % fk == fk - 1
+                    clast = ks == ksc - 1
                     inflight['mma'][w] += 1
 
-                    def complete(w=w, yb=yb, g=g, last=last):
+                    def complete(w=w, yb=yb, g=g, gr=gr, glast=glast, clast=clast):
                         inflight['mma'][w] -= 1
                         y_busy[(w, yb)] -= 1
                         commit[w][yb].arrive()
-                        if last:
-                            mma_done.add((w, g))
+                        if glast:
+                            mma_done.add((w, gr))
                             chunk[w].arrive()
+                        if clast:
+                            chunk_done.add((w, g))
                     later(complete, warp=w)
                 readers[g] -= 1
             yield from sync(0)
             gc += nch
-            gs += nch * KSC
+            gs += nch * ksc
+            gg += nch * ngr
             yield from sync(0)
         if drain:                            # commit + wait: all of this warp's MMAs completed
             yield from drain_wait(lambda: inflight['mma'][w] == 0)
         yield from sync(0)
 
-    agents = [helper(h) for h in range(NH)] + [tile(w) for w in range(NW)]
+    agents = [helper(h) for h in range(NH)] + [tile(w) for w in range(nw)]
     alive = list(range(len(agents)))
     steps = 0
     while alive:
@@ -266,6 +280,39 @@ def test_protocol_is_hazard_free(seed):
     # a CTA's contiguous share of the points may hold no tile at all (fewer
     # points than CTAs): n_tiles = 0 only drains
     assert not run_schedule(seed, n_tiles=seed % 4, nch=1 + (seed // 3) % 6)
+
+
+@pytest.mark.parametrize('seed', range(40))
+@pytest.mark.parametrize('nw,ksc,fk', [(3, 8, 2), (5, 4, 4)])
+def test_wide_kernel_protocol_is_hazard_free(seed, nw, ksc, fk):
+    # the wide kernel: fewer tile warps, fold groups of fk k-steps within a
+    # chunk (chunk and fold barriers advance once per group)
+    assert not run_schedule(seed, n_tiles=seed % 4, nch=1 + (seed // 3) % 5, nw=nw, ksc=ksc, fk=fk)
+
+
+@pytest.mark.parametrize('seed', range(20))
+def test_wide_kernel_timeouts_end_after_a_drain(seed):
+    nt, nch = 1 + seed % 3, 1 + (seed // 3) % 5
+    latency = 30 if seed % 2 else 400
+    span = run_schedule(seed, nt, nch, latency=latency, clock=True, nw=3, ksc=8, fk=2)
+    r = random.Random(seed)
+    at = r.randrange(span) if seed % 3 else max(0, span - r.randrange(1, latency))
+    run_schedule(seed, nt, nch, latency=latency, timeout_at=at, nw=3, ksc=8, fk=2)
+
+
+def test_wide_kernel_wrong_fold_wait_is_caught():
+    # with fold groups of 4 k-steps, waiting on the per-buffer commit barrier
+    # of the group's last k-step instead of the group barrier lets a fold run
+    # early (with groups of 2 k-steps each buffer barrier advances once per
+    # group, and that wait would be as good as the group barrier)
+    hits = 0
+    for seed in range(6):
+        try:
+            run_schedule(seed, n_tiles=2, nch=3, fold_wait='buffer', max_steps=60_000, nw=5, ksc=4, fk=4)
+        except Hazard as e:
+            assert 'before its MMAs completed' in str(e)
+            hits += 1
+    assert hits > 0
 
 
 @pytest.mark.parametrize('seed', range(30))
