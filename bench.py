@@ -714,9 +714,10 @@ def main():
 
 def other_workloads(rv, names, precision, steps, dev, flush):
     """Throughput of the evaluation call on the other workloads (the
-    autotuner's kernels, the workload's macro field, micro states after
-    three mixed evaluations from a fresh state), for the record: evals/s
-    and ms per call, with the kernels used."""
+    autotuner's kernels, the workload's macro field, the main leg's
+    mid-Newton micro states), for the record: evals/s and ms per call, the
+    kernels used, and the error of the timed form against the float64 form
+    at every point."""
     import torch
     out = {}
     stream = torch.cuda.current_stream()
@@ -739,8 +740,15 @@ def other_workloads(rv, names, precision, steps, dev, flush):
         rv.macro_gradient(mesh, u, Fbar)
         q, s, S, U = h.zero_state(n)
         Pbar, dPdF, rnorm, status = h.outputs(n)
-        for _ in range(3):
-            rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=precision)
+        # the mid-Newton state of the main leg: micro states converged at Fbar
+        # by float64 evaluations, then q perturbed by 1e-3 of its size
+        for _ in range(4):
+            rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision='fp64')
+        g = torch.Generator(device='cpu').manual_seed(syn.SEED_BASE + 710)
+        pert = torch.randn(q.shape, generator=g, dtype=torch.float64).to(dev)
+        q += 1e-3 * q.abs().amax(dim=1, keepdim=True) * pert * (q != 0)
+        s.zero_()
+        S.zero_()
         torch.cuda.synchronize()
         st0 = [x.clone() for x in (q, s, S, U)]
         tot = 0.0
@@ -755,10 +763,31 @@ def other_workloads(rv, names, precision, steps, dev, flush):
             e1.synchronize()
             tot += e0.elapsed_time(e1)
         ms = tot / steps
+        failed = int((status != 0).sum().item())
+        # accuracy at full size: the timed form against the float64 form from
+        # the same micro states, every point
+        acc = None
+        if precision == 'mixed':
+            outs = []
+            for prec in ('fp64', 'mixed'):
+                for x, y in zip((q, s, S, U), st0):
+                    x.copy_(y)
+                rv.rve_rom_eval_batch(h, Fbar, q, s, S, U, Pbar, dPdF, rnorm, status, type=types, precision=prec)
+                outs.append((Pbar.clone(), dPdF.clone(), status.clone()))
+            (P64, C64, s64), (Pm, Cm, sm) = outs
+            ok = (s64 == 0) & (sm == 0)
+            ep = ((Pm - P64).abs().amax(1) / P64.abs().amax(1))[ok]
+            ec = ((Cm - C64).abs().amax((1, 2)) / C64.abs().amax((1, 2)))[ok]
+            acc = {"Pbar_rel_err_max": float(ep.max().item()), "dPdF_rel_err_max": float(ec.max().item()),
+                   "Pbar_rel_err_p99": float(torch.quantile(ep.float(), 0.99).item()),
+                   "points_over_1e-8": int((ep > 1e-8).sum().item()), "points": int(ok.sum().item()),
+                   "against": "float64 GPU form from the same micro states, every point"}
         out[name] = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms, "points": n,
-                     "failed_points": int((status != 0).sum().item()),
+                     "failed_points": failed,
                      "kernels": [rv.rve_rom_kernel_info(h, t, precision)[0] for t in range(len(roms))],
-                     "workload": wl['desc'], "state": "three mixed evaluations from a fresh state"}
+                     "accuracy_vs_fp64_form": acc,
+                     "workload": wl['desc'],
+                     "state": "mid-Newton (micro states converged by 4 float64 evaluations, q perturbed by 1e-3 |q|)"}
         h.destroy()
         mesh.destroy()
     return out
