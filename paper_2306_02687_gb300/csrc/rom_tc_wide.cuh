@@ -69,6 +69,7 @@ struct TcWidePlan {
     static_assert(NAR == 32 || NAR == 64, "32 or 64 mode rows per point");
     static_assert(CI * PPT == 32, "one law evaluation per lane and chunk");
     static_assert(CI % EPS == 0 && KSC % FK == 0, "a chunk holds whole fold groups");
+    static_assert(FK >= 2, "a group's first two k-steps are issued together");
     static_assert(NN % 16 == 0 && NW >= 1, "fold in blocks of 16 columns");
     static_assert(NP * G <= NHT, "one homogenized-stress entry per helper thread");
     static_assert(TCOLS <= 512, "TMEM holds 512 columns");
@@ -578,27 +579,40 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
                     }
                     tc::fence_proxy_async();
                     __syncwarp();
+                    // the first k-step of a fold group is issued together with
+                    // the second: both A buffers are built (the second needs
+                    // only the MMAs of the previous group's last k-step) while
+                    // the helpers still fold the previous group
+                    const int kg = ks % FK;
+                    if (kg == 0) continue;
                     if (lane == 0) {
-                        if (ks == 0) wait(&b_bx[b], (g >> 1) & 1);
+                        if (ks == 1) wait(&b_bx[b], (g >> 1) & 1);
                         // the accumulators of the previous fold group were folded
-                        if (ks % FK == 0 && gr >= 1) wait(b_fold, (gr - 1) & 1);
+                        if (kg == 1 && gr >= 1) wait(b_fold, (gr - 1) & 1);
                     }
                     if (lane == 0 && *s_err == 0) {
                         tc::fence_after_sync();
-                        const uint32_t ba = tc::smem_u32(s_BX + b * (PL::BXBUF / 4) + ks * 2 * (PL::BXPART / 4));
-                        const uint64_t bdh = tc::smem_desc(ba, 128, 256);
-                        const uint64_t bdl = tc::smem_desc(ba + (uint32_t)PL::BXPART, 128, 256);
-                        const uint64_t adh = tc::smem_desc(tc::smem_u32(Yh), 2048, 128);
-                        const uint64_t adl = tc::smem_desc(tc::smem_u32(Yl), 2048, 128);
                         const uint32_t dt = tbase + warp * NN;
-                        // a group's first MMA starts the accumulator fresh in the
-                        // first two groups of a tile; later it adds onto the
-                        // fold's compensation term
-                        tc::mma_tf32(dt, adh, bdh, idesc, (ks % FK > 0 || gl >= 2) ? 1u : 0u);
-                        tc::mma_tf32(dt, adh, bdl, idesc, 1u);
-                        tc::mma_tf32(dt, adl, bdh, idesc, 1u);
-                        tc::mma_commit(&mbar[yb]);
-                        if (ks % FK == FK - 1) tc::mma_commit(&b_chunk[warp]);  // the whole fold group
+#pragma unroll
+                        for (int q2 = (kg == 1 ? 1 : 0); q2 >= 0; --q2) {
+                            // k-step ks - q2 of this chunk (k-step s - q2 of the CTA)
+                            const int ki = ks - q2;
+                            const int ybi = (int)((s - q2) & 1);
+                            const float *Yhi = yw + ybi * 2048, *Ylo = Yhi + 1024;
+                            const uint32_t ba = tc::smem_u32(s_BX + b * (PL::BXBUF / 4) + ki * 2 * (PL::BXPART / 4));
+                            const uint64_t bdh = tc::smem_desc(ba, 128, 256);
+                            const uint64_t bdl = tc::smem_desc(ba + (uint32_t)PL::BXPART, 128, 256);
+                            const uint64_t adh = tc::smem_desc(tc::smem_u32(Yhi), 2048, 128);
+                            const uint64_t adl = tc::smem_desc(tc::smem_u32(Ylo), 2048, 128);
+                            // a group's first MMA starts the accumulator fresh in the
+                            // first two groups of a tile; later it adds onto the
+                            // fold's compensation term
+                            tc::mma_tf32(dt, adh, bdh, idesc, (ki % FK > 0 || gl >= 2) ? 1u : 0u);
+                            tc::mma_tf32(dt, adh, bdl, idesc, 1u);
+                            tc::mma_tf32(dt, adl, bdh, idesc, 1u);
+                            tc::mma_commit(&mbar[ybi]);
+                        }
+                        if (kg == FK - 1) tc::mma_commit(&b_chunk[warp]);  // the whole fold group
                     }
                     __syncwarp();
                 }

@@ -62,12 +62,14 @@ class Hazard(AssertionError):
 
 
 def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeout_at=None, drain=True,
-                 latency=30, clock=False, nw=NW, ksc=KSC, fk=None):
+                 latency=30, clock=False, nw=NW, ksc=KSC, fk=None, defer=False):
     """timeout_at: the first wait still blocked at or after this model time
     runs out.  Returns True when a timeout was injected; raises Hazard.
     nw tile warps, ksc k-steps per chunk, a fold every fk k-steps (default:
     once per chunk, the warp-specialized kernel; the wide kernel folds every
-    2 or 4 k-steps with 3 or 5 tile warps)."""
+    2 or 4 k-steps with 3 or 5 tile warps).  defer: a group's first k-step
+    is issued together with its second, after both A buffers are built (the
+    wide kernel)."""
     fk = ksc if fk is None else fk
     ngr = ksc // fk
     rng = random.Random(seed)
@@ -85,6 +87,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
     last_mma = {}      # per warp: completion time of its latest MMA group
     now = [0]
     mma_done, mma_issued, folded = set(), set(), {}   # per (warp, fold group)
+    pending = set()                                    # (warp, k-step) built, MMAs not issued yet
     chunk_done = set()                                 # per (warp, chunk)
     wp_written, res_done, landed, readers, y_busy = {}, {}, set(), {}, {}
 
@@ -222,30 +225,41 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                     if s >= 2:
                         yield from wait(commit[w][yb], ((s - 2) >> 1) & 1)
                     check(y_busy.get((w, yb), 0) == 0, 'A buffer rewritten while MMAs read it')
+                    check((w, s) not in pending, 'A buffer rewritten before its MMAs were issued')
+                    pending.add((w, s))
                     yield
-                    if ks == 0:
+                    kg = ks % fk
+                    if defer and kg == 0:
+                        continue                     # issued with the next k-step
+                    first = (kg == 1) if defer else (kg == 0)
+                    if ks == (1 if defer else 0):
                         yield from wait(bx[b], (g >> 1) & 1)
-                    if ks % fk == 0 and gr >= 1:
+                    if first and gr >= 1:
                         yield from wait(fold, (gr - 1) & 1)
                         check(len(folded.get((w, gr - 1), ())) == NH, 'MMAs of group %d before the fold' % gr)
                     if err[0]:                   # no MMA is issued after a timeout
+                        pending.discard((w, s))
+                        pending.discard((w, s - 1))
                         continue
-                    mma_issued.add((w, gr))
-                    y_busy[(w, yb)] = y_busy.get((w, yb), 0) + 1
-                    glast = ks % fk == fk - 1
-                    clast = ks == ksc - 1
-                    inflight['mma'][w] += 1
+                    for si in ((s - 1, s) if (defer and kg == 1) else (s,)):
+                        pending.discard((w, si))
+                        ybi = si & 1
+                        mma_issued.add((w, gr))
+                        y_busy[(w, ybi)] = y_busy.get((w, ybi), 0) + 1
+                        glast = si == s and kg == fk - 1
+                        clast = si == s and ks == ksc - 1
+                        inflight['mma'][w] += 1
 
-                    def complete(w=w, yb=yb, g=g, gr=gr, glast=glast, clast=clast):
-                        inflight['mma'][w] -= 1
-                        y_busy[(w, yb)] -= 1
-                        commit[w][yb].arrive()
-                        if glast:
-                            mma_done.add((w, gr))
-                            chunk[w].arrive()
-                        if clast:
-                            chunk_done.add((w, g))
-                    later(complete, warp=w)
+                        def complete(w=w, yb=ybi, g=g, gr=gr, glast=glast, clast=clast):
+                            inflight['mma'][w] -= 1
+                            y_busy[(w, yb)] -= 1
+                            commit[w][yb].arrive()
+                            if glast:
+                                mma_done.add((w, gr))
+                                chunk[w].arrive()
+                            if clast:
+                                chunk_done.add((w, g))
+                        later(complete, warp=w)
                 readers[g] -= 1
             yield from sync(0)
             gc += nch
@@ -287,17 +301,17 @@ def test_protocol_is_hazard_free(seed):
 def test_wide_kernel_protocol_is_hazard_free(seed, nw, ksc, fk):
     # the wide kernel: fewer tile warps, fold groups of fk k-steps within a
     # chunk (chunk and fold barriers advance once per group)
-    assert not run_schedule(seed, n_tiles=seed % 4, nch=1 + (seed // 3) % 5, nw=nw, ksc=ksc, fk=fk)
+    assert not run_schedule(seed, n_tiles=seed % 4, nch=1 + (seed // 3) % 5, nw=nw, ksc=ksc, fk=fk, defer=True)
 
 
 @pytest.mark.parametrize('seed', range(20))
 def test_wide_kernel_timeouts_end_after_a_drain(seed):
     nt, nch = 1 + seed % 3, 1 + (seed // 3) % 5
     latency = 30 if seed % 2 else 400
-    span = run_schedule(seed, nt, nch, latency=latency, clock=True, nw=3, ksc=8, fk=2)
+    span = run_schedule(seed, nt, nch, latency=latency, clock=True, nw=3, ksc=8, fk=2, defer=True)
     r = random.Random(seed)
     at = r.randrange(span) if seed % 3 else max(0, span - r.randrange(1, latency))
-    run_schedule(seed, nt, nch, latency=latency, timeout_at=at, nw=3, ksc=8, fk=2)
+    run_schedule(seed, nt, nch, latency=latency, timeout_at=at, nw=3, ksc=8, fk=2, defer=True)
 
 
 def test_wide_kernel_wrong_fold_wait_is_caught():
@@ -308,7 +322,7 @@ def test_wide_kernel_wrong_fold_wait_is_caught():
     hits = 0
     for seed in range(6):
         try:
-            run_schedule(seed, n_tiles=2, nch=3, fold_wait='buffer', max_steps=60_000, nw=5, ksc=4, fk=4)
+            run_schedule(seed, n_tiles=2, nch=3, fold_wait='buffer', max_steps=60_000, nw=5, ksc=4, fk=4, defer=True)
         except Hazard as e:
             assert 'before its MMAs completed' in str(e)
             hits += 1
