@@ -472,8 +472,12 @@ def main():
     torch.cuda.synchronize()
     pn = Pbar.abs().amax(dim=1).clamp_min(1e-300)
     cn = dPdF.abs().amax(dim=(1, 2)).clamp_min(1e-300)
-    p_err = ((P1 - Pbar).abs().amax(dim=1) / pn).max().item()
+    p_pt = (P1 - Pbar).abs().amax(dim=1) / pn
+    p_err = p_pt.max().item()
     c_err = ((C1 - dPdF).abs().amax(dim=(1, 2)) / cn).max().item()
+    p_err_type = None
+    if types is not None:      # per RVE type of a mixed batch
+        p_err_type = {wl['roms'][t]: float(p_pt[types == t].max().item()) for t in range(len(roms))}
 
     # accuracy of the timed form against the float64 oracle, per output, on
     # 256 sampled points that carry oracle mid-Newton states (the workload's
@@ -703,6 +707,7 @@ def main():
         "other_form": {"precision": other, "value": world * n / (ms_other * 1e-3), "ms_per_step": ms_other},
         "speedup_vs_fp64_form": (ms_other / ms_step) if args.precision == 'mixed' else 1.0,
         "accuracy_vs_fp64_form": {"Pbar_rel_err_max": p_err, "dPdF_rel_err_max": c_err,
+                                  "Pbar_rel_err_max_per_type": p_err_type,
                                   "points": n, "note": "every point, against the GPU float64 form"},
         "accuracy_vs_oracle": acc,
     }
@@ -778,7 +783,12 @@ def other_workloads(rv, names, precision, steps, dev, flush):
             ok = (s64 == 0) & (sm == 0)
             ep = ((Pm - P64).abs().amax(1) / P64.abs().amax(1))[ok]
             ec = ((Cm - C64).abs().amax((1, 2)) / C64.abs().amax((1, 2)))[ok]
+            per_type = None
+            if types is not None:
+                tk = types[ok]
+                per_type = {wl['roms'][t]: float(ep[tk == t].max().item()) for t in range(len(roms))}
             acc = {"Pbar_rel_err_max": float(ep.max().item()), "dPdF_rel_err_max": float(ec.max().item()),
+                   "Pbar_rel_err_max_per_type": per_type,
                    "Pbar_rel_err_p99": float(torch.quantile(ep.float(), 0.99).item()),
                    "points_over_1e-8": int((ep > 1e-8).sum().item()), "points": int(ok.sum().item()),
                    "against": "float64 GPU form from the same micro states, every point"}

@@ -89,7 +89,7 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, C
             add(RV_SYM(2, 36, 6, 12, 16, float), "simt-symmetric <2,36> 6x6 blocks, 12 points x 16 ECM", 1);
             add(RV_SYM(2, 36, 6, 12, 8, float), "simt-symmetric <2,36> 6x6 blocks, 12 points x 8 ECM", 1);
             add(RV_FUSED(2, 36, 9, 9, 16, 8, float), "simt-fused <2,36> 16 points x 8 ECM", 1);
-            add(RV_TCW(2, 36, 8, 4), "tcgen05-tf32x3 wide <2,36> 5 tile + 4 helper warps, 20 points x 8 ECM, fold per 4 k-steps", 2);
+            add(RV_TCW(2, 36, 8, 2), "tcgen05-tf32x3 wide <2,36> 5 tile + 4 helper warps, 20 points x 8 ECM, fold per 2 k-steps", 2);
         } else if (n <= 64) {
             add(RV_SYM(2, 72, 6, 3, 16, float), "simt-symmetric <2,72> 6x6 blocks, 3 points x 16 ECM", 1);
             add(RV_FUSED(2, 72, 9, 9, 4, 8, float), "simt-fused <2,72> 4 points x 8 ECM", 1);

@@ -297,7 +297,7 @@ def test_protocol_is_hazard_free(seed):
 
 
 @pytest.mark.parametrize('seed', range(40))
-@pytest.mark.parametrize('nw,ksc,fk', [(3, 8, 2), (5, 4, 4)])
+@pytest.mark.parametrize('nw,ksc,fk', [(3, 8, 2), (5, 4, 2), (5, 4, 4)])
 def test_wide_kernel_protocol_is_hazard_free(seed, nw, ksc, fk):
     # the wide kernel: fewer tile warps, fold groups of fk k-steps within a
     # chunk (chunk and fold barriers advance once per group)
