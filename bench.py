@@ -857,28 +857,7 @@ def newton_leg(rv, h, mesh, wl, u_host, Fbar, q, s, S, U, Pbar, dPdF, rnorm, sta
            "residual_after": {"R_free_max": float(nr[0]), "R_prescribed_max": float(nr[1]),
                               "micro_r_max": float(nr[2])},
            "bc": "%s: %d prescribed DOFs held at the synthetic field's values" % (wl['mesh'][0], len(dofs)),
-           "solve": "macro_solve: block-Jacobi preconditioned CG, relative tolerance 1e-12",
-           "solve_form": {1: "grid-wide cooperative kernel", 2: "one 16-CTA cluster, system in shared memory"}[
-               rv.macro_mesh_set_solver(mesh, 0)]}
-    # the same last system solved by each form, for the record
-    forms = {}
-    for kind in (1, 2):
-        try:
-            rv.macro_mesh_set_solver(mesh, kind)
-        except RuntimeError:
-            continue
-        t = 0.0
-        for _ in range(3):
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            _, inf1 = rv.macro_solve(mesh, Kv, R, free, du=du, tol=1e-12)
-            f1.record(stream)
-            f1.synchronize()
-            t += f0.elapsed_time(f1)
-        i1 = inf1.cpu().numpy()
-        forms[{1: "grid", 2: "cluster"}[kind]] = {"ms": t / 3, "cg_iterations": int(i1[0]), "status": int(i1[2])}
-    rv.macro_mesh_set_solver(mesh, 0)
-    out["solve_forms_last_system"] = forms
+           "solve": "macro_solve: block-Jacobi preconditioned CG, relative tolerance 1e-12"}
     # the same Newton iteration captured in one CUDA graph
     try:
         restore()

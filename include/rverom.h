@@ -273,20 +273,6 @@ int macro_residual_norms(rverom_mesh_t m, const double *R, const uint8_t *free_m
 int macro_solve(rverom_mesh_t m, const double *Kvals, const double *R, const uint8_t *free_mask, double tol,
                 int32_t max_iter, double *u, double *du, double *info, void *stream);
 
-/* Which form of macro_solve runs on this mesh (same algorithm, same
- * status codes, results equal up to the order of the floating-point sums):
- *   kind 1: the cooperative grid-wide kernel above (any size);
- *   kind 2: one thread-block cluster of 16 CTAs whose shared memory holds
- *           the whole system (each CTA a node range: its CSR rows, a copy of
- *           the search direction gathered through distributed shared memory,
- *           cluster-wide sums in rank order); only when the mesh fits, which
- *           macro_mesh_create decides (c2's 8 448-DOF plate fits);
- *   kind 0: kind 2 when the mesh fits, else kind 1 (the default).
- * *in_use (host, may be NULL) receives the kind macro_solve will run.
- * Errors: RVEROM_ERR_ARG for another kind, RVEROM_ERR_UNSUPPORTED for kind 2
- * on a mesh that does not fit. */
-int macro_mesh_set_solver(rverom_mesh_t m, int32_t kind, int32_t *in_use);
-
 /* Largest m~ over the types of a handle (the ECM-point stride of the
  * history arrays of rve_rom_eval_batch_j2). */
 int rve_rom_mmax(rverom_t h, int32_t *mmax);

@@ -11,7 +11,7 @@ Python entry points (thin marshalling over librverom.so, see api.py):
   rve_rom_create, rve_rom_set_moduli, rve_rom_autotune, rve_rom_select_kernel,
                   rve_rom_kernel_info, rve_rom_eval_batch, rve_rom_adjoint,
   macro_mesh_create, macro_gradient, macro_assemble, macro_residual_norms,
-                  macro_solve (global Newton correction on the device), macro_mesh_set_solver,
+                  macro_solve (global Newton correction on the device),
                   macro_gradient_range, macro_assemble_range (one element shard)
   parallel: element sharding and the all-reduce of the assembled system
   rve_rom_eval_batch_j2, rve_rom_mmax (history-dependent J2 law at the ECM points)
@@ -23,8 +23,7 @@ from .api import (FP64, MIXED, RomHandle, MeshHandle, load_rom_file, rve_rom_cre
                   rve_rom_set_moduli, rve_rom_autotune, rve_rom_select_kernel,
                   rve_rom_kernel_info, rve_rom_eval_batch, rve_rom_adjoint, rve_rom_adjoint_static,
                   macro_mesh_create,
-                  macro_gradient, macro_assemble, macro_residual_norms, macro_solve, macro_mesh_set_solver,
-                  rve_rom_mmax,
+                  macro_gradient, macro_assemble, macro_residual_norms, macro_solve, rve_rom_mmax,
                   macro_gradient_range, macro_assemble_range,
                   rve_rom_eval_batch_j2, rve_rom_biot_cauchy,
                   surrogate_linear_eval, paths_kmeans, rverom_df_log, rverom_peak_probe)

@@ -45,7 +45,6 @@ SIGNATURES = {
     'macro_assemble_range': (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     'macro_residual_norms': (c_int, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     'macro_solve': (c_int, [c_vp, c_vp, c_vp, c_vp, c_dbl, c_int, c_vp, c_vp, c_vp, c_vp]),
-    'macro_mesh_set_solver': (c_int, [c_vp, c_int, P(c_int)]),
     'rve_rom_mmax': (c_int, [c_vp, P(c_int)]),
     'rve_rom_eval_batch_j2': (c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                       P(c_dbl), c_vp, c_vp, c_vp, c_vp, c_vp]),

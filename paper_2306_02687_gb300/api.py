@@ -290,15 +290,6 @@ def macro_residual_norms(m, R, free_mask, rnorm, out, stream=None):
         _stream(stream)), 'macro_residual_norms')
 
 
-def macro_mesh_set_solver(m, kind=0):
-    """Form of macro_solve on this mesh: 0 automatic, 1 grid-wide kernel,
-    2 one thread-block cluster (when the system fits its shared memory).
-    Returns the form that macro_solve will run."""
-    used = ctypes.c_int32()
-    _native.check(_native.lib().macro_mesh_set_solver(m.ptr, int(kind), ctypes.byref(used)), 'macro_mesh_set_solver')
-    return used.value
-
-
 def macro_solve(m, Kvals, R, free_mask, u=None, du=None, info=None, tol=1e-12, max_iter=20000, stream=None):
     """Newton correction of the macro problem on the device: K du = -R on the
     free DOFs (du = 0 on the prescribed ones), u += du when u is given.

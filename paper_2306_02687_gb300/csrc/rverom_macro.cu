@@ -1,7 +1,6 @@
 // rverom_macro.cu -- macro level of the FE^2 step: deformation gradient at
 // the macro integration points, element residual/stiffness assembly from
 // (Pbar, dPdF) (Eq. 6 of the paper and its linearization), convergence norms.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,13 +30,6 @@ struct rverom_mesh_s {
     double *part = nullptr;      // device [2][3][solve_blocks] per-block partial sums (double-buffered)
     unsigned *sync = nullptr;    // device [4]: grid-barrier count and generation, error flag
     int solve_blocks = 0;
-    // single-cluster form of the solve (the whole system in the shared
-    // memory of one thread-block cluster): feasibility and layout
-    int cl_blocks = 0;           // CTAs of the cluster (0: the system does not fit)
-    int cl_cap_nnz = 0;          // largest CSR slice of one CTA
-    int cl_max_rows = 0;         // largest row range of one CTA
-    size_t cl_smem = 0;          // dynamic shared memory per CTA
-    int solver = 0;              // 0 automatic, 1 grid-wide, 2 single cluster
 };
 
 namespace {
@@ -677,315 +669,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg(SolveArgs a) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// The same preconditioned CG on one thread-block cluster whose CTAs hold the
-// whole system in shared memory: CTA c owns a contiguous node range (its rows
-// of K, their column indices, its rows of r, p, s, x, w and its nodes' block
-// inverses) and a full copy of the search direction u, whose other slices it
-// gathers from the other CTAs' shared memory (distributed shared memory)
-// after every update.  The three sums of an iteration are reduced over the
-// cluster in rank order (the same in every CTA, so the result does not
-// depend on timing).  Two cluster barriers per iteration, both hardware
-// barriers (no polling); a latency-bound solve of a system this small then
-// runs on CL_MAX SMs instead of a grid-wide barrier over all of them.
-constexpr int CL_THREADS = 1024;
-constexpr int CL_MAX = 16;
-
-__device__ double block_sum_cl(double v, double *sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < CL_THREADS / 32; ++k) t += sh[k];
-    return t;
-}
-
-// dynamic shared memory layout of the cluster solve, in 8-byte words
-struct ClLayout {
-    int64_t uf, kv, r, p, s, x, w, minv, part, sums, cv, words;
-    __host__ __device__ ClLayout(int64_t n_dof, int cap_nnz, int max_rows, int d) {
-        uf = 0;                               // u, whole vector [n_dof]
-        kv = uf + n_dof;                      // K values of the own rows [cap_nnz]
-        r = kv + cap_nnz;                     // own rows of r, p, s, x, w [max_rows] each
-        p = r + max_rows;
-        s = p + max_rows;
-        x = s + max_rows;
-        w = x + max_rows;
-        minv = w + max_rows;                  // block inverses of the own nodes [max_rows * d]
-        part = minv + (int64_t)max_rows * d;  // this CTA's partial sums [4]
-        sums = part + 4;                      // the cluster's sums [4]
-        cv = sums + 4;                        // column indices of the own rows, int32 [cap_nnz]
-        words = cv + (cap_nnz + 1) / 2;
-    }
-};
-
-template <int D>
-__global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(SolveArgs a, int cap_nnz, int max_rows) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    const unsigned rank = cl.block_rank(), nc = cl.num_blocks();
-    extern __shared__ __align__(16) double csm[];
-    const ClLayout L(a.n_dof, cap_nnz, max_rows, D);
-    double *uf = csm + L.uf, *Kv = csm + L.kv, *rv_ = csm + L.r, *pv = csm + L.p, *sv = csm + L.s;
-    double *xv = csm + L.x, *wv = csm + L.w, *Mv = csm + L.minv, *part = csm + L.part, *sums = csm + L.sums;
-    int32_t *cv = reinterpret_cast<int32_t *>(csm + L.cv);
-    __shared__ double sh[32];
-    const int tid = threadIdx.x;
-    const int64_t nb = a.n_nodes * rank / nc, ne = a.n_nodes * (rank + 1) / nc;
-    const int64_t rb = nb * D;
-    const int nrow = (int)((ne - nb) * D);
-    const int32_t e0 = a.rowp[rb];
-    const int nnz = a.rowp[rb + nrow] - e0;  // <= cap_nnz (checked at mesh set-up)
-    for (int e = tid; e < nnz; e += CL_THREADS) {
-        Kv[e] = a.K[e0 + e];
-        cv[e] = a.col[e0 + e];
-    }
-    constexpr int LPR = D == 2 ? 8 : 16;  // lanes per row of the sparse product
-    constexpr int RPW = 32 / LPR;
-    const int lane = tid & 31, sub = lane % LPR, warp = tid >> 5;
-    // w = K u on the own free rows, partial (w, u)
-    auto spmv = [&]() {
-        double wu = 0.0;
-        for (int r0 = warp * RPW; r0 < nrow; r0 += (CL_THREADS / 32) * RPW) {
-            const int lr = r0 + lane / LPR;
-            double v = 0.0;
-            const bool in = lr < nrow;
-            if (in && a.free_mask[rb + lr]) {
-                const int b0 = a.rowp[rb + lr] - e0, b1 = a.rowp[rb + lr + 1] - e0;
-                for (int e = b0 + sub; e < b1; e += LPR) v += Kv[e] * uf[cv[e]];
-            }
-#pragma unroll
-            for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, LPR);
-            if (sub == 0 && in) {
-                wv[lr] = v;
-                wu += v * uf[rb + lr];
-            }
-        }
-        return wu;
-    };
-    // the other CTAs' slices of u into the own copy
-    auto gather = [&]() {
-        for (unsigned q = 0; q < nc; ++q) {
-            if (q == rank) continue;
-            const int64_t qb = a.n_nodes * q / nc * D, qe = a.n_nodes * (q + 1) / nc * D;
-            const double *uq = cl.map_shared_rank(uf, q);
-            for (int64_t i = qb + tid; i < qe; i += CL_THREADS) uf[i] = uq[i];
-        }
-        __syncthreads();
-    };
-    // sums of three partials over the cluster, in rank order
-    auto cluster_sums = [&](double x0, double x1, double x2, double (&out)[3]) {
-        x0 = block_sum_cl(x0, sh);
-        x1 = block_sum_cl(x1, sh);
-        x2 = block_sum_cl(x2, sh);
-        if (tid == 0) {
-            part[0] = x0;
-            part[1] = x1;
-            part[2] = x2;
-        }
-        cl.sync();
-        if (tid == 0) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-            for (unsigned q = 0; q < nc; ++q) {
-                const double *pq = cl.map_shared_rank(part, q);
-                s0 += pq[0];
-                s1 += pq[1];
-                s2 += pq[2];
-            }
-            sums[0] = s0;
-            sums[1] = s1;
-            sums[2] = s2;
-        }
-        __syncthreads();
-        out[0] = sums[0];
-        out[1] = sums[1];
-        out[2] = sums[2];
-    };
-    // preconditioner and start (as in k_pcg): b = -R on the free DOFs,
-    // x = 0, r = b, u = M r, p = s = 0
-    double bb = 0.0, ru = 0.0;
-    for (int64_t nd = nb + tid; nd < ne; nd += CL_THREADS) {
-        const int ln = (int)(nd - nb);
-        double Bk[D * D], Bi[D * D];
-        bool fr[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) fr[i] = a.free_mask[nd * D + i] != 0;
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int k = 0; k < D; ++k)
-                Bk[i * D + k] = (fr[i] && fr[k]) ? a.K[a.dpos[nd * D + i] + k] : (i == k ? 1.0 : 0.0);
-        double det;
-        if (D == 2) {
-            det = Bk[0] * Bk[3] - Bk[1] * Bk[2];
-            Bi[0] = Bk[3] / det;
-            Bi[1] = -Bk[1] / det;
-            Bi[2] = -Bk[2] / det;
-            Bi[3] = Bk[0] / det;
-        } else {
-            det = Bk[0] * (Bk[4] * Bk[8] - Bk[5] * Bk[7]) - Bk[1] * (Bk[3] * Bk[8] - Bk[5] * Bk[6]) +
-                  Bk[2] * (Bk[3] * Bk[7] - Bk[4] * Bk[6]);
-            Bi[0] = (Bk[4] * Bk[8] - Bk[5] * Bk[7]) / det;
-            Bi[1] = (Bk[2] * Bk[7] - Bk[1] * Bk[8]) / det;
-            Bi[2] = (Bk[1] * Bk[5] - Bk[2] * Bk[4]) / det;
-            Bi[3] = (Bk[5] * Bk[6] - Bk[3] * Bk[8]) / det;
-            Bi[4] = (Bk[0] * Bk[8] - Bk[2] * Bk[6]) / det;
-            Bi[5] = (Bk[2] * Bk[3] - Bk[0] * Bk[5]) / det;
-            Bi[6] = (Bk[3] * Bk[7] - Bk[4] * Bk[6]) / det;
-            Bi[7] = (Bk[1] * Bk[6] - Bk[0] * Bk[7]) / det;
-            Bi[8] = (Bk[0] * Bk[4] - Bk[1] * Bk[3]) / det;
-        }
-        if (!(det > 0.0) || !isfinite(det)) {
-#pragma unroll
-            for (int c = 0; c < D * D; ++c) Bi[c] = (c % (D + 1) == 0) ? 1.0 : 0.0;
-        }
-#pragma unroll
-        for (int c = 0; c < D * D; ++c) Mv[ln * D * D + c] = Bi[c];
-        double r0[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            r0[i] = fr[i] ? -a.R[nd * D + i] : 0.0;
-            bb += r0[i] * r0[i];
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            double ui = 0.0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) ui += Bi[i * D + k] * r0[k];
-            ui = fr[i] ? ui : 0.0;
-            const int lr = ln * D + i;
-            rv_[lr] = r0[i];
-            uf[rb + lr] = ui;
-            pv[lr] = 0.0;
-            sv[lr] = 0.0;
-            xv[lr] = 0.0;
-            ru += r0[i] * ui;
-        }
-    }
-    cl.sync();  // every CTA has started and published its slice of u
-    gather();
-    const double wu0 = spmv();
-    double sm[3];
-    cluster_sums(ru, wu0, bb, sm);
-    double gam = sm[0], del = sm[1];
-    bb = sm[2];
-    double rr = bb, alpha = gam / del, beta = 0.0;
-    int it = 0, status = 1;
-    const double tol2 = a.tol * a.tol * bb;
-    for (;;) {
-        if (rr <= tol2) {
-            status = 0;
-            break;
-        }
-        if (it >= a.max_iter) break;
-        if (!(del > 0.0) || !(gam > 0.0) || !isfinite(alpha) || !(alpha > 0.0)) {
-            status = 2;
-            break;
-        }
-        // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M r
-        double pr = 0.0, prr = 0.0;
-        for (int64_t nd = nb + tid; nd < ne; nd += CL_THREADS) {
-            const int ln = (int)(nd - nb);
-            double r1[D];
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                const int lr = ln * D + i;
-                const double pk = uf[rb + lr] + beta * pv[lr];
-                const double sk = wv[lr] + beta * sv[lr];
-                pv[lr] = pk;
-                sv[lr] = sk;
-                xv[lr] += alpha * pk;
-                r1[i] = rv_[lr] - alpha * sk;
-                rv_[lr] = r1[i];
-                prr += r1[i] * r1[i];
-            }
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                double ui = 0.0;
-#pragma unroll
-                for (int k = 0; k < D; ++k) ui += Mv[ln * D * D + i * D + k] * r1[k];
-                ui = a.free_mask[nd * D + i] ? ui : 0.0;
-                uf[rb + ln * D + i] = ui;
-                pr += r1[i] * ui;
-            }
-        }
-        cl.sync();  // every slice of u updated (and every CTA done with the last sums)
-        gather();
-        const double pwu = spmv();
-        cluster_sums(pr, pwu, prr, sm);
-        ++it;
-        rr = sm[2];
-        const double gn = sm[0];
-        del = sm[1];
-        beta = gn / gam;
-        gam = gn;
-        alpha = gn / (del - beta * gn / alpha);
-    }
-    for (int lr = tid; lr < nrow; lr += CL_THREADS) {
-        const double v = xv[lr];
-        a.du[rb + lr] = v;
-        if (a.u) a.u[rb + lr] += v;
-    }
-    if (rank == 0 && tid == 0) {
-        a.info[0] = (double)it;
-        a.info[1] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-        a.info[2] = (double)status;
-    }
-    cl.sync();  // no CTA leaves while another may still read its shared memory
-}
-
-// whether (and with what layout) the system fits one cluster
-void cluster_setup(rverom_mesh_s *m, const std::vector<int32_t> &rowp32) {
-    m->cl_blocks = 0;
-    const int d = m->dim;
-    const int nc = CL_MAX;
-    if (m->n_nodes < nc) return;
-    int cap = 0, rows = 0;
-    for (int c = 0; c < nc; ++c) {
-        const int64_t nb = m->n_nodes * c / nc, ne = m->n_nodes * (c + 1) / nc;
-        cap = std::max(cap, rowp32[ne * d] - rowp32[nb * d]);
-        rows = std::max(rows, (int)((ne - nb) * d));
-    }
-    const ClLayout L(m->n_dof, cap, rows, d);
-    const size_t bytes = (size_t)L.words * 8;
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return;
-    if (bytes + 1024 > (size_t)optin) return;
-    auto kern = d == 2 ? (void *)k_pcg_cluster<2> : (void *)k_pcg_cluster<3>;
-    // the largest allowance, so that meshes of different sizes can share the kernel
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nc);
-    cfg.blockDim = dim3(CL_THREADS);
-    cfg.dynamicSmemBytes = bytes;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = nc;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
-        cudaGetLastError();
-        return;
-    }
-    m->cl_blocks = nc;
-    m->cl_cap_nnz = cap;
-    m->cl_max_rows = rows;
-    m->cl_smem = bytes;
-}
-
 bool solve_setup(rverom_mesh_s *m, const std::vector<int32_t> &rowp32, const std::vector<int32_t> &dpos) {
     const int d = m->dim;
     int occ = 0;
@@ -996,7 +679,6 @@ bool solve_setup(rverom_mesh_s *m, const std::vector<int32_t> &rowp32, const std
     // plate 152 blocks took 18 us per iteration, 37 blocks 27 us), at most
     // SOLVE_THREADS (one partial per thread in grid_sums)
     m->solve_blocks = m->n_sm < SOLVE_THREADS ? m->n_sm : SOLVE_THREADS;
-    cluster_setup(m, rowp32);
     const size_t nw = (size_t)m->n_dof * 6 + (size_t)m->n_nodes * d * d;
     return cudaMalloc(&m->rowp, rowp32.size() * 4) == cudaSuccess &&
            cudaMalloc(&m->colv, m->col.size() * 4) == cudaSuccess &&
@@ -1037,24 +719,6 @@ extern "C" int macro_solve(rverom_mesh_t m, const double *Kvals, const double *R
     a.minv = a.x + m->n_dof;
     a.part = m->part;
     a.sync = m->sync;
-    if (m->solver == 2 || (m->solver == 0 && m->cl_blocks > 0)) {
-        if (m->cl_blocks == 0) return RVEROM_ERR_UNSUPPORTED;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)m->cl_blocks);
-        cfg.blockDim = dim3(CL_THREADS);
-        cfg.dynamicSmemBytes = m->cl_smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)m->cl_blocks;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaError_t e = m->dim == 2 ? cudaLaunchKernelEx(&cfg, k_pcg_cluster<2>, a, m->cl_cap_nnz, m->cl_max_rows)
-                                    : cudaLaunchKernelEx(&cfg, k_pcg_cluster<3>, a, m->cl_cap_nnz, m->cl_max_rows);
-        return e == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
-    }
     // cooperative launch: every block is resident, so the grid barriers are
     // safe (and bounded in time all the same)
     cudaLaunchConfig_t cfg = {};
@@ -1069,12 +733,4 @@ extern "C" int macro_solve(rverom_mesh_t m, const double *Kvals, const double *R
     cfg.numAttrs = 1;
     cudaError_t e = m->dim == 2 ? cudaLaunchKernelEx(&cfg, k_pcg<2>, a) : cudaLaunchKernelEx(&cfg, k_pcg<3>, a);
     return e == cudaSuccess ? RVEROM_OK : RVEROM_ERR_CUDA;
-}
-
-extern "C" int macro_mesh_set_solver(rverom_mesh_t m, int32_t kind, int32_t *in_use) {
-    if (!m || kind < 0 || kind > 2) return RVEROM_ERR_ARG;
-    if (kind == 2 && m->cl_blocks == 0) return RVEROM_ERR_UNSUPPORTED;
-    m->solver = kind;
-    if (in_use) *in_use = (kind == 0) ? (m->cl_blocks > 0 ? 2 : 1) : kind;
-    return RVEROM_OK;
 }

@@ -57,13 +57,9 @@ def _system(kind):
     return m, X, R, Kv, free
 
 
-@pytest.mark.parametrize('solver', [1, 2])
 @pytest.mark.parametrize('kind', ['rect', 'plate', 'box'])
-def test_macro_solve_matches_direct_solve(kind, solver):
-    # both forms of the solve: the grid-wide cooperative kernel and the
-    # single-cluster one (the system in the shared memory of 16 CTAs)
+def test_macro_solve_matches_direct_solve(kind):
     m, X, R, Kv, free = _system(kind)
-    assert rv.macro_mesh_set_solver(m, solver) == solver
     u0 = syn.perturbation(syn.SEED_BASE + 62, X.shape, 0.01)
     u = T(u0)
     du, info = rv.macro_solve(m, Kv, R, T(free, torch.uint8), u=u, tol=1e-14)
@@ -75,16 +71,14 @@ def test_macro_solve_matches_direct_solve(kind, solver):
     fi = np.nonzero(free)[0]
     ref = spla.spsolve(K[fi][:, fi].tocsc(), -R.cpu().numpy()[fi])
     got = du.cpu().numpy()
-    print(kind, 'solver', solver, 'n_dof', m.n_dof, 'iterations', int(it))
+    print(kind, 'n_dof', m.n_dof, 'iterations', int(it))
     assert np.abs(got[fi] - ref).max() <= 1e-9 * np.abs(ref).max()
     assert np.all(got[free == 0] == 0.0)
     assert np.array_equal(u.cpu().numpy().ravel(), u0.ravel() + got)
 
 
-@pytest.mark.parametrize('solver', [1, 2])
-def test_macro_solve_status_codes(solver):
+def test_macro_solve_status_codes():
     m, X, R, Kv, free = _system('rect')
-    rv.macro_mesh_set_solver(m, solver)
     fr = T(free, torch.uint8)
     du, info = rv.macro_solve(m, Kv, R, fr, tol=1e-14, max_iter=1)
     torch.cuda.synchronize()
@@ -103,26 +97,6 @@ def test_macro_solve_status_codes(solver):
     d2, i2 = rv.macro_solve(m, Kv, R, fr, tol=1e-12)
     torch.cuda.synchronize()
     assert torch.equal(d1, d2)
-
-
-def test_solver_forms_agree_and_selection():
-    # the two forms solve the same system to the same tolerance; the
-    # automatic choice is the cluster form where the system fits
-    m, X, R, Kv, free = _system('plate')
-    fr = T(free, torch.uint8)
-    assert rv.macro_mesh_set_solver(m, 0) == 2
-    out = {}
-    for solver in (1, 2):
-        rv.macro_mesh_set_solver(m, solver)
-        du, info = rv.macro_solve(m, Kv, R, fr, tol=1e-13)
-        torch.cuda.synchronize()
-        out[solver] = (du.clone().cpu().numpy(), info.cpu().numpy())
-    d1, d2 = out[1][0], out[2][0]
-    assert out[1][1][2] == 0 and out[2][1][2] == 0
-    assert abs(out[1][1][0] - out[2][1][0]) <= 2            # the same iteration up to rounding
-    assert np.abs(d1 - d2).max() <= 1e-10 * np.abs(d1).max()
-    with pytest.raises(RuntimeError):
-        rv.macro_mesh_set_solver(m, 3)
 
 
 @pytest.mark.parametrize('precision', ['fp64', 'mixed'])
