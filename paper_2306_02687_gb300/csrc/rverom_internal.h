@@ -144,7 +144,7 @@ cudaError_t launch_tc_ws(const EvalArgs &a, int n_sm, int64_t max_points, cudaSt
 template <int D, int NA, int CI, int FK>
 cudaError_t launch_tc_wide(const EvalArgs &a, int n_sm, int64_t max_points, cudaStream_t st, int *grid_out) {
     using PL = TcWidePlan<D, NA, CI, FK>;
-    constexpr int CT = NA <= 36 ? 32 : 16, TPP = 256 / CT;
+    constexpr int CT = NA <= 36 ? 32 : 8, TPP = 256 / CT;
     using CP = CondPlan<D, NA, CT, TPP>;
     static_assert(CP::bytes <= 227 * 1024, "condensation shared memory");
     if (!a.t.Bimg || a.t.img_nn != PL::NN || !a.cond) return cudaErrorInvalidValue;
