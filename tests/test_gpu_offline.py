@@ -107,3 +107,39 @@ def test_offline_pipeline_matches_oracle():
     eo, eg = np.abs(Po - Pf).max(), np.abs(Pg - Pf).max()
     print('hyper-ROM error vs full integration: oracle %.2e, gpu %.2e' % (eo, eg))
     assert eg <= max(3 * eo, 1e-6 * np.abs(Pf).max())
+
+
+def test_offline_stage_at_the_24_mode_scale():
+    # the offline stage on the GPU for the RVE of the 24-mode workload (48 x 48
+    # Q4, four seeded inclusions, 20 training paths x 10 steps up to 0.15, 24
+    # modes, 200 ECM points: the recipe of the stored ROM, which the oracle
+    # built); the GPU-built hyper-ROM must approximate the full-order RVE as
+    # well as the oracle-built one at seeded test stretches
+    import importlib.util
+    import os
+    from oracle import reduced
+    from conftest import rom_path
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location('make_roms', os.path.join(here, 'golden', 'make_roms.py'))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    c = mk.CONFIGS['c2']
+    model = mk.build_rve(c)
+    paths = syn.training_paths(syn.SEED_BASE + c['seed'], 2, c['paths'], c['steps'], c['eps'])
+    rom_g, st = offline.build_hyper_rom(c['n'], model.phase, MOD, paths, c['modes'], c['ecm'],
+                                        rng=syn.rng(syn.SEED_BASE + 330))
+    print('48 x 48 RVE offline stage on the GPU:', {k: round(v, 3) for k, v in st['times'].items()},
+          'ECM points', len(rom_g['w']), 'ecm info', st['info_ecm'])
+    assert np.all(st['info_snap'][:, 3] == 0) and np.all(st['info_lin'][:, 3] == 0)
+    w = rom_g['w']
+    assert np.all(w > 0) and abs(w.sum() - 1.0) <= 1e-8 and 100 <= len(w) <= c['ecm']
+    rg = reduced.Rom(rom_g['B'], w, rom_g['phase'], rom_g['moduli'], 1.0)
+    ro = reduced.Rom.load(rom_path('c2'))
+    Fs = syn.fbar_batch(syn.SEED_BASE + 331, 2, 3, 0.1, 0.3)
+    for Fb in Fs:
+        Pf = model.solve(Fb)[1]
+        Pg = reduced.converge_point(rg, Fb)[0]['Pbar']
+        Po = reduced.converge_point(ro, Fb)[0]['Pbar']
+        eg, eo = np.abs(Pg - Pf).max() / np.abs(Pf).max(), np.abs(Po - Pf).max() / np.abs(Pf).max()
+        print('hyper-ROM error against the full-order RVE: GPU-built %.2e, oracle-built %.2e' % (eg, eo))
+        assert eg <= max(3 * eo, 5e-3)
