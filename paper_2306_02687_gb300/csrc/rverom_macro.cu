@@ -466,15 +466,36 @@ __device__ double block_sum(double v, double *sh) {
     return t;
 }
 
+// sums over this block's threads of NV values each, in one shared-memory
+// round (every thread gets the sums; sh holds 8 NV doubles)
+template <int NV>
+__device__ void block_sums(double (&v)[NV], double *sh) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[8 * k + w] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < SOLVE_THREADS / 32; ++j) t += sh[8 * k + j];
+        v[k] = t;
+    }
+}
+
 // sums of the per-block partials of NV quantities (written by other blocks:
 // read past L1), one partial per thread and the same order in every block
 template <int NV>
 __device__ void grid_sums(const double *part, unsigned nblk, double *sh, double (&out)[NV]) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double v = threadIdx.x < nblk ? __ldcg(part + k * nblk + threadIdx.x) : 0.0;
-        out[k] = block_sum(v, sh + 8 * k);
-    }
+    for (int k = 0; k < NV; ++k) out[k] = threadIdx.x < nblk ? __ldcg(part + k * nblk + threadIdx.x) : 0.0;
+    block_sums<NV>(out, sh);
 }
 
 template <int D>
@@ -631,11 +652,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg(SolveArgs a) {
             }
         }
         double *pt = a.part + (size_t)((it + 1) & 1) * 3 * nblk;  // partials of this iteration (double-buffered)
-        pr = block_sum(pr, sh);
-        prr = block_sum(prr, sh + 8);
-        if (threadIdx.x == 0) {
-            pt[blockIdx.x] = pr;
-            pt[2 * nblk + blockIdx.x] = prr;
+        {
+            double v2[2] = {pr, prr};
+            block_sums<2>(v2, sh);
+            if (threadIdx.x == 0) {
+                pt[blockIdx.x] = v2[0];
+                pt[2 * nblk + blockIdx.x] = v2[1];
+            }
         }
         if (!(ok = grid_barrier(a.sync, nblk))) break;  // u complete
         double pwu = 0.0;
