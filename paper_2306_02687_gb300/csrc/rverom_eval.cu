@@ -59,10 +59,11 @@ bool supported_modes(int dim, int n) { return n >= 1 && ((dim == 2 && n <= 64) |
 #define RV_TCW(D, NA, CI, FK) &launch_tc_wide<D, NA, CI, FK>
 
 int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, CandInfo *info) {
-    LaunchFn c[4] = {};
-    CandInfo ci[4] = {};
+    LaunchFn c[RVEROM_MAX_CANDIDATES] = {};
+    CandInfo ci[RVEROM_MAX_CANDIDATES] = {};
     int k = 0;
     auto add = [&](LaunchFn f, const char *name, int launches) {
+        if (k >= RVEROM_MAX_CANDIDATES) return;  // at most as many as the tuning report holds
         c[k] = f;
         ci[k] = CandInfo{name, launches};
         ++k;
@@ -550,7 +551,7 @@ extern "C" int rve_rom_autotune(rverom_t h, int32_t precision, int64_t n_sample,
                     for (int64_t i = 0; i < n && valid; ++i) valid = st_host[(size_t)i] == RVEROM_STATUS_OK;
                 }
             }
-            if (ms_out) ms_out[t * RVEROM_MAX_CANDIDATES + c] = valid ? tbest : -2.0f;
+            if (ms_out && c < RVEROM_MAX_CANDIDATES) ms_out[t * RVEROM_MAX_CANDIDATES + c] = valid ? tbest : -2.0f;
             if (valid && tbest < best) {
                 best = tbest;
                 bi = c;
