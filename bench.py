@@ -792,8 +792,35 @@ def other_workloads(rv, names, precision, steps, dev, flush):
                    "Pbar_rel_err_p99": float(torch.quantile(ep.float(), 0.99).item()),
                    "points_over_1e-8": int((ep > 1e-8).sum().item()), "points": int(ok.sum().item()),
                    "against": "float64 GPU form from the same micro states, every point"}
+        j2leg = None
+        if name == 'c4' and wl['d'] == 2 and len(roms) == 1:
+            # the history-dependent law of Example 1 at the ECM points
+            # (small-strain J2, yield 0.01 E, hardening 0.016 E in the matrix,
+            # elastic inclusions; float64 form), from the same micro states
+            # with virgin histories
+            mm = rv.rve_rom_mmax(h)
+            hin = torch.zeros(n, mm, 7, dtype=torch.float64, device=dev)
+            hout = torch.empty_like(hin)
+            plastic = np.array([[[0.01, 0.016], [np.inf, 0.0]]])
+            tj = 0.0
+            for rep in range(4):
+                for x, y in zip((q, s, S, U), st0):
+                    x.copy_(y)
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rv.rve_rom_eval_batch_j2(h, Fbar, q, s, S, U, hin, hout, plastic, Pbar, dPdF, rnorm, status)
+                e1.record(stream)
+                e1.synchronize()
+                if rep > 0:
+                    tj += e0.elapsed_time(e1)
+            tj /= 3
+            plastic_pts = int((hout[..., 6] > 0).any(dim=1).sum().item())
+            j2leg = {"value": n / (tj * 1e-3), "unit": UNIT, "ms_per_call": tj,
+                     "failed_points": int((status != 0).sum().item()), "points_yielding": plastic_pts,
+                     "form": "float64, one warp per macro point (rve_rom_eval_batch_j2)"}
         out[name] = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms, "points": n,
-                     "failed_points": failed,
+                     "failed_points": failed, "j2_plasticity": j2leg,
                      "kernels": [rv.rve_rom_kernel_info(h, t, precision)[0] for t in range(len(roms))],
                      "accuracy_vs_fp64_form": acc,
                      "workload": wl['desc'],
