@@ -38,6 +38,8 @@
 //   drain      every MMA of every tile warp completed (before TMEM is freed)
 #pragma once
 
+#include <type_traits>
+
 #include "rom_tc.cuh"
 
 namespace rverom {
@@ -64,6 +66,8 @@ struct TcWidePlan {
     static constexpr int RPH = (NP * NQ + NHT - 1) / NHT;  // residual rows per helper thread
     static constexpr int TCOLS = 2 * NW * NN;       // accumulator + running sum
     static constexpr int TALLOC = TCOLS <= 256 ? 256 : 512;
+    static constexpr int SOFF = TALLOC / 2;         // running sums: a 32-column-aligned offset
+    static constexpr int FBW = NN > 64 ? 32 : 16;   // fold block width (32 spills at 9 warps)
     static constexpr int NKF = G * (G + 1) / 2;     // K_FF entries (symmetric)
     static_assert(D == 2, "planar RVEs (two ECM points per k-step)");
     static_assert(NAR == 32 || NAR == 64, "32 or 64 mode rows per point");
@@ -73,6 +77,7 @@ struct TcWidePlan {
     static_assert(NN % 16 == 0 && NW >= 1, "fold in blocks of 16 columns");
     static_assert(NP * G <= NHT, "one homogenized-stress entry per helper thread");
     static_assert(TCOLS <= 512, "TMEM holds 512 columns");
+    static_assert(NW * NN <= SOFF && SOFF % 32 == 0, "accumulators, then running sums from column SOFF");
     // byte offsets
     static constexpr size_t YWARP = 4 * 4096;  // per tile warp: [2 buffers][hi|lo][2 kg][16 rg][8][4] floats
     static constexpr size_t o_Y = 0;
@@ -101,6 +106,12 @@ struct TcWidePlan {
     static constexpr size_t bytes = tc_al(o_slot + 8);
     static_assert(bytes <= 227 * 1024, "shared memory");
 };
+
+// 16 or 32 consecutive TMEM columns of the warp's lane quarter
+__device__ __forceinline__ void tmem_ldw(uint32_t ta, float (&v)[16]) { tc::tmem_ld16(ta, v); }
+__device__ __forceinline__ void tmem_ldw(uint32_t ta, float (&v)[32]) { tc::tmem_ld32(ta, v); }
+__device__ __forceinline__ void tmem_stw(uint32_t ta, const float (&v)[16]) { tc::tmem_st16(ta, v); }
+__device__ __forceinline__ void tmem_stw(uint32_t ta, const float (&v)[32]) { tc::tmem_st32(ta, v); }
 
 template <int D, int NA, int CI, int FK>
 __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide_kernel(EvalArgs a) {
@@ -254,34 +265,47 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
                         if (t * PPT >= nlive) break;  // tiles without points (their rows are never read)
                         const int row = t * 128 + qd * 32 + lane;
                         const int p = row / NAR, jr = row % NAR;
-#pragma unroll
-                        for (int cb = 0; cb < NN / 16; ++cb) {
-                            const uint32_t ca = tbase + lanes + t * NN + cb * 16;
-                            float va[16], vs[16];
-                            tc::tmem_ld16(ca, va);
-                            if (kahan) tc::tmem_ld16(ca + NW * NN, vs);
+                        // blocks of 32 columns on 32-column boundaries (one load
+                        // wait per block for the accumulator and the running sum,
+                        // which sit SOFF columns apart), 16-column edge blocks
+                        auto fold_block = [&](auto wc, int c0) {
+                            constexpr int W = decltype(wc)::value;
+                            const uint32_t ca = tbase + lanes + t * NN + c0;
+                            float va[W], vs[W];
+                            tmem_ldw(ca, va);
+                            if (kahan) tmem_ldw(ca + PL::SOFF, vs);
                             tc::tmem_wait_ld();
                             if (kahan) {
 #pragma unroll
-                                for (int c = 0; c < 16; ++c) {
+                                for (int c = 0; c < W; ++c) {
                                     const float tt = __fadd_rn(vs[c], va[c]);
                                     vs[c] = __fsub_rn(va[c], __fsub_rn(tt, vs[c]));  // -(compensation)
                                     va[c] = tt;
                                 }
-                                if (!last) tc::tmem_st16(ca, vs);
+                                if (!last) tmem_stw(ca, vs);
                             }
                             if (!last) {
-                                tc::tmem_st16(ca + NW * NN, va);
+                                tmem_stw(ca + PL::SOFF, va);
                             } else if (jr < n && p < nlive) {
                                 // lane jr holds column jr of M: entries (col, jr), col >= jr
                                 // (K and K_qF; K_FF comes from the tile warps)
                                 float *rm = ws + (t0 + p) * CR::W + CR::o_M;
 #pragma unroll
-                                for (int c = 0; c < 16; ++c) {
-                                    const int col = cb * 16 + c;
+                                for (int c = 0; c < W; ++c) {
+                                    const int col = c0 + c;
                                     if (col < NA && col >= jr) rm[tri(col, jr)] = va[c];
                                 }
                             }
+                        };
+                        if constexpr (PL::FBW == 32) {
+                            const int lead = (t * NN) & 16;  // the tile's first column is 0 or 16 mod 32
+                            if (lead) fold_block(std::integral_constant<int, 16>{}, 0);
+                            for (int cb = 0; cb < (NN - lead) / 32; ++cb)
+                                fold_block(std::integral_constant<int, 32>{}, lead + cb * 32);
+                            if ((NN - lead) % 32) fold_block(std::integral_constant<int, 16>{}, NN - 16);
+                        } else {
+#pragma unroll
+                            for (int cb = 0; cb < NN / 16; ++cb) fold_block(std::integral_constant<int, 16>{}, cb * 16);
                         }
                     }
                     if (!last) tc::tmem_wait_st();
