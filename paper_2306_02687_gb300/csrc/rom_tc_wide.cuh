@@ -56,7 +56,7 @@ struct TcWidePlan {
     static constexpr int PPT = 128 / NAR;           // points per 128-row tile
     static constexpr int NN = (NA + 15) / 16 * 16;  // MMA N (columns of Bext)
     static constexpr int NW = 512 / (2 * NN);       // tile warps = tiles
-    static constexpr int NH = 4;                    // helper warps (one per TMEM lane quarter)
+    static constexpr int NH = NN > 64 ? 8 : 4;      // helper warps (NH / 4 per TMEM lane quarter)
     static constexpr int NT = 32 * (NW + NH);
     static constexpr int NHT = 32 * NH;             // helper threads
     static constexpr int NP = NW * PPT;             // points per CTA tile
@@ -67,7 +67,7 @@ struct TcWidePlan {
     static constexpr int TCOLS = 2 * NW * NN;       // accumulator + running sum
     static constexpr int TALLOC = TCOLS <= 256 ? 256 : 512;
     static constexpr int SOFF = TALLOC / 2;         // running sums: a 32-column-aligned offset
-    static constexpr int FBW = NN > 64 ? 32 : 16;   // fold block width (32 spills at 9 warps)
+    static constexpr int FBW = 16;                  // fold block width
     static constexpr int NKF = G * (G + 1) / 2;     // K_FF entries (symmetric)
     static_assert(D == 2, "planar RVEs (two ECM points per k-step)");
     static_assert(NAR == 32 || NAR == 64, "32 or 64 mode rows per point");
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
             tc::named_bar(0, NT);  // A
             dacc rdacc[2 * RPH];
             df pudf{0.0f, 0.0f};
-            const int ht = tid - NW * 32, qd = warp & 3;
+            const int ht = tid - NW * 32, qd = warp & 3, hh = (warp - NW) >> 2;
             const uint32_t lanes = (uint32_t)(qd * 32) << 16;
             // residual rows o = ht + NHT u: point o / NQ, mode o % NQ
             int bo[RPH], wo[RPH];
@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
                     for (int w2 = 0; w2 < NW; ++w2) wait(&b_chunk[w2], gr & 1);
                     __syncwarp();
                     tc::fence_after_sync();
+                    int fb = 0;  // fold blocks of this group so far
                     for (int t = 0; t < NW; ++t) {
                         if (t * PPT >= nlive) break;  // tiles without points (their rows are never read)
                         const int row = t * 128 + qd * 32 + lane;
@@ -270,6 +271,10 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
                         // which sit SOFF columns apart), 16-column edge blocks
                         auto fold_block = [&](auto wc, int c0) {
                             constexpr int W = decltype(wc)::value;
+                            // the lane quarter's helper warps take its blocks in turn
+                            if constexpr (NH > 4) {
+                                if (fb++ % (NH / 4) != hh) return;
+                            }
                             const uint32_t ca = tbase + lanes + t * NN + c0;
                             float va[W], vs[W];
                             tmem_ldw(ca, va);
