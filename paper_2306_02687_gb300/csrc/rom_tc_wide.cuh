@@ -5,9 +5,11 @@
 //
 // Same roles, arithmetic and workspace records as eval_tc_ws_kernel
 // (rom_tc_ws.cuh): tile warps evaluate the law (double-float), build their
-// tile's A rows and issue its three TF32 MMA passes per k-step; four helper
-// warps fold the TMEM accumulators (Kahan), accumulate the float64-accurate
-// residual and homogenized stress, stage the tables and write the records.
+// tile's A rows and issue its three TF32 MMA passes per k-step; helper warps
+// (one or two per TMEM lane quarter) fold the TMEM accumulators (Kahan),
+// tile by tile, releasing each tile warp as its tile is done, accumulate the
+// float64-accurate residual and homogenized stress, stage the tables and
+// write the records.
 // What changes with the width:
 //  - A-operand rows are the modes only (NAR = n~max rows per point: 32 or
 //    64, so 4 or 2 points per 128-row tile).  The MMA yields K and K_qF
@@ -20,9 +22,9 @@
 //  - The accumulators are folded every FK k-steps (a fold group; 3 FK MMAs
 //    per fold) instead of once per chunk: the accumulation error of the wide
 //    systems needs a fold every 4 (32 modes) or 2 (64 modes) k-steps for the
-//    1e-8 stress gate.  Barriers chunk[w] and fold then advance once per
+//    1e-8 stress gate.  Barriers chunk[w] and fold[w] then advance once per
 //    fold group.
-//  - No register reallocation: with 224 or 288 threads every warp has the
+//  - No register reallocation: with 288 or 352 threads every warp has the
 //    registers it needs at launch.
 // Hand-offs (mbarriers, every wait bounded by tc::WAIT_LIMIT_NS; after the
 // first timeout of a CTA no wait blocks, nothing more is issued, the tile's
@@ -34,11 +36,9 @@
 //   chunk[w]   MMAs of a fold group of tile warp w completed
 //   wp[b]      w_i P_i of a chunk written by every tile warp (buffer b)
 //   res[b]     residual of the chunk in buffer b done (w P buffer free)
-//   fold       accumulators of the last fold group folded (accumulators free)
+//   fold[w]    accumulators of tile w's last fold group folded (free again)
 //   drain      every MMA of every tile warp completed (before TMEM is freed)
 #pragma once
-
-#include <type_traits>
 
 #include "rom_tc.cuh"
 
@@ -67,7 +67,6 @@ struct TcWidePlan {
     static constexpr int TCOLS = 2 * NW * NN;       // accumulator + running sum
     static constexpr int TALLOC = TCOLS <= 256 ? 256 : 512;
     static constexpr int SOFF = TALLOC / 2;         // running sums: a 32-column-aligned offset
-    static constexpr int FBW = 16;                  // fold block width
     static constexpr int NKF = G * (G + 1) / 2;     // K_FF entries (symmetric)
     static_assert(D == 2, "planar RVEs (two ECM points per k-step)");
     static_assert(NAR == 32 || NAR == 64, "32 or 64 mode rows per point");
@@ -99,19 +98,13 @@ struct TcWidePlan {
     static constexpr size_t o_Udf = tc_al(o_dU + (size_t)NP * NS * 8);
     static constexpr size_t o_flag = tc_al(o_Udf + 2 * (size_t)NP * G * 4);
     static constexpr size_t o_pidx = o_flag + NP * 4;
-    // mbarriers: bx[2], commit[NW][2], staged[2], wp[2], res[2], fold, chunk[NW], drain
-    static constexpr int NBAR = 2 + 2 * NW + 2 + 2 + 2 + 1 + NW + 1;
+    // mbarriers: bx[2], commit[NW][2], staged[2], wp[2], res[2], fold[NW], chunk[NW], drain
+    static constexpr int NBAR = 2 + 2 * NW + 2 + 2 + 2 + NW + NW + 1;
     static constexpr size_t o_bar = tc_al(o_pidx + NP * 4);
     static constexpr size_t o_slot = o_bar + NBAR * 8;
     static constexpr size_t bytes = tc_al(o_slot + 8);
     static_assert(bytes <= 227 * 1024, "shared memory");
 };
-
-// 16 or 32 consecutive TMEM columns of the warp's lane quarter
-__device__ __forceinline__ void tmem_ldw(uint32_t ta, float (&v)[16]) { tc::tmem_ld16(ta, v); }
-__device__ __forceinline__ void tmem_ldw(uint32_t ta, float (&v)[32]) { tc::tmem_ld32(ta, v); }
-__device__ __forceinline__ void tmem_stw(uint32_t ta, const float (&v)[16]) { tc::tmem_st16(ta, v); }
-__device__ __forceinline__ void tmem_stw(uint32_t ta, const float (&v)[32]) { tc::tmem_st32(ta, v); }
 
 template <int D, int NA, int CI, int FK>
 __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide_kernel(EvalArgs a) {
@@ -138,7 +131,7 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
     int *s_pidx = reinterpret_cast<int *>(smem + PL::o_pidx);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + PL::o_bar);
     uint64_t *b_bx = s_bar, *b_commit = s_bar + 2, *b_staged = b_commit + 2 * NW;
-    uint64_t *b_wp = b_staged + 2, *b_res = b_wp + 2, *b_fold = b_res + 2, *b_chunk = b_fold + 1;
+    uint64_t *b_wp = b_staged + 2, *b_res = b_wp + 2, *b_fold = b_res + 2, *b_chunk = b_fold + NW;
     uint64_t *b_drain = b_chunk + NW;
     uint32_t *s_slot = reinterpret_cast<uint32_t *>(smem + PL::o_slot);
     volatile int *s_err = reinterpret_cast<volatile int *>(smem + PL::o_slot + 4);
@@ -166,8 +159,10 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
             tc::mbar_init(&b_wp[b], NW);
             tc::mbar_init(&b_res[b], NH);
         }
-        tc::mbar_init(b_fold, NH);
-        for (int w = 0; w < NW; ++w) tc::mbar_init(&b_chunk[w], 1);
+        for (int w = 0; w < NW; ++w) {
+            tc::mbar_init(&b_fold[w], NH);
+            tc::mbar_init(&b_chunk[w], 1);
+        }
         tc::mbar_init(b_drain, NW);
         tc::mbar_init_fence();
         *s_err = 0;
@@ -246,39 +241,45 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
             for (int ch = 0; ch < nch; ++ch) {
                 const uint32_t g = gc + ch;
                 const int b = g & 1;
-                // folds of the chunk's groups: wait for the group's last commit
-                // of every tile warp, fold lane quarter qd of every tile,
+                // folds of the chunk's groups, tile by tile: wait for the group's
+                // last commit of the tile warp, fold lane quarter qd of its tile,
                 // Kahan-compensated (the negated compensation goes into the
-                // accumulator, onto which the next group's MMAs add); the last
-                // fold of the tile writes the augmented systems to the workspace
+                // accumulator, onto which the next group's MMAs add), release the
+                // tile warp; the last fold of the tile writes the augmented
+                // systems to the workspace
                 for (int gi = 0; gi < NGR; ++gi) {
                     const uint32_t gr = gg + (uint32_t)(ch * NGR + gi);  // CTA-wide fold group
                     const bool last = (ch == nch - 1) && (gi == NGR - 1);
                     const bool kahan = ch * NGR + gi > 0;
-                    // one phase per group; tile warp w cannot commit group gr + 1
-                    // before this fold released the accumulators, so phase gr is
-                    // the barrier's current phase or the one before it
-                    for (int w2 = 0; w2 < NW; ++w2) wait(&b_chunk[w2], gr & 1);
-                    __syncwarp();
-                    tc::fence_after_sync();
                     int fb = 0;  // fold blocks of this group so far
                     for (int t = 0; t < NW; ++t) {
-                        if (t * PPT >= nlive) break;  // tiles without points (their rows are never read)
+                        // one phase per group; tile warp t cannot commit group
+                        // gr + 1 before this fold released its accumulators, so
+                        // phase gr is the barrier's current phase or the one before
+                        wait(&b_chunk[t], gr & 1);
+                        __syncwarp();
+                        tc::fence_after_sync();
+                        // tiles without points: their rows are never read, but the
+                        // tile warp's barriers advance all the same
+                        if (t * PPT >= nlive) {
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(&b_fold[t]);
+                            continue;
+                        }
                         const int row = t * 128 + qd * 32 + lane;
                         const int p = row / NAR, jr = row % NAR;
-                        // blocks of 32 columns on 32-column boundaries (one load
-                        // wait per block for the accumulator and the running sum,
-                        // which sit SOFF columns apart), 16-column edge blocks
-                        auto fold_block = [&](auto wc, int c0) {
-                            constexpr int W = decltype(wc)::value;
+                        // blocks of 16 columns of the accumulator and its running
+                        // sum (SOFF columns further on)
+                        auto fold_block = [&](int c0) {
+                            constexpr int W = 16;
                             // the lane quarter's helper warps take its blocks in turn
                             if constexpr (NH > 4) {
                                 if (fb++ % (NH / 4) != hh) return;
                             }
                             const uint32_t ca = tbase + lanes + t * NN + c0;
                             float va[W], vs[W];
-                            tmem_ldw(ca, va);
-                            if (kahan) tmem_ldw(ca + PL::SOFF, vs);
+                            tc::tmem_ld16(ca, va);
+                            if (kahan) tc::tmem_ld16(ca + PL::SOFF, vs);
                             tc::tmem_wait_ld();
                             if (kahan) {
 #pragma unroll
@@ -287,10 +288,10 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
                                     vs[c] = __fsub_rn(va[c], __fsub_rn(tt, vs[c]));  // -(compensation)
                                     va[c] = tt;
                                 }
-                                if (!last) tmem_stw(ca, vs);
+                                if (!last) tc::tmem_st16(ca, vs);
                             }
                             if (!last) {
-                                tmem_stw(ca + PL::SOFF, va);
+                                tc::tmem_st16(ca + PL::SOFF, va);
                             } else if (jr < n && p < nlive) {
                                 // lane jr holds column jr of M: entries (col, jr), col >= jr
                                 // (K and K_qF; K_FF comes from the tile warps)
@@ -302,21 +303,13 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
                                 }
                             }
                         };
-                        if constexpr (PL::FBW == 32) {
-                            const int lead = (t * NN) & 16;  // the tile's first column is 0 or 16 mod 32
-                            if (lead) fold_block(std::integral_constant<int, 16>{}, 0);
-                            for (int cb = 0; cb < (NN - lead) / 32; ++cb)
-                                fold_block(std::integral_constant<int, 32>{}, lead + cb * 32);
-                            if ((NN - lead) % 32) fold_block(std::integral_constant<int, 16>{}, NN - 16);
-                        } else {
 #pragma unroll
-                            for (int cb = 0; cb < NN / 16; ++cb) fold_block(std::integral_constant<int, 16>{}, cb * 16);
-                        }
+                        for (int cb = 0; cb < NN / 16; ++cb) fold_block(cb * 16);
+                        if (!last) tc::tmem_wait_st();
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&b_fold[t]);
                     }
-                    if (!last) tc::tmem_wait_st();
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(b_fold);
                 }
                 // a4: residual and homogenized stress of chunk ch (double-float)
                 wait(&b_wp[b], (g >> 1) & 1);
@@ -617,7 +610,7 @@ __global__ void __launch_bounds__(TcWidePlan<D, NA, CI, FK>::NT, 1) eval_tc_wide
                     if (lane == 0) {
                         if (ks == 1) wait(&b_bx[b], (g >> 1) & 1);
                         // the accumulators of the previous fold group were folded
-                        if (kg == 1 && gr >= 1) wait(b_fold, (gr - 1) & 1);
+                        if (kg == 1 && gr >= 1) wait(&b_fold[warp], (gr - 1) & 1);
                     }
                     if (lane == 0 && *s_err == 0) {
                         tc::fence_after_sync();

@@ -62,14 +62,17 @@ class Hazard(AssertionError):
 
 
 def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeout_at=None, drain=True,
-                 latency=30, clock=False, nw=NW, ksc=KSC, fk=None, defer=False):
+                 latency=30, clock=False, nw=NW, ksc=KSC, fk=None, defer=False, nh=NH, tile_fold=None):
     """timeout_at: the first wait still blocked at or after this model time
     runs out.  Returns True when a timeout was injected; raises Hazard.
     nw tile warps, ksc k-steps per chunk, a fold every fk k-steps (default:
     once per chunk, the warp-specialized kernel; the wide kernel folds every
     2 or 4 k-steps with 3 or 5 tile warps).  defer: a group's first k-step
     is issued together with its second, after both A buffers are built (the
-    wide kernel)."""
+    wide kernel).  nh helper warps.  tile_fold: one fold barrier per tile,
+    arrived at as each tile is folded ('own': each tile warp waits on its
+    tile's barrier, the wide kernel; 'first': every tile warp waits on tile
+    0's barrier, a wrong wait); None: one fold barrier after all tiles."""
     fk = ksc if fk is None else fk
     ngr = ksc // fk
     rng = random.Random(seed)
@@ -78,11 +81,12 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
     bx = [Barrier(1), Barrier(1)]
     commit = [[Barrier(1), Barrier(1)] for _ in range(nw)]
     chunk = [Barrier(1) for _ in range(nw)]
-    staged = [Barrier(NH), Barrier(NH)]   # one arrival per helper warp's copies
+    staged = [Barrier(nh), Barrier(nh)]   # one arrival per helper warp's copies
     wp = [Barrier(nw), Barrier(nw)]
-    res = [Barrier(NH), Barrier(NH)]
-    fold = Barrier(NH)
-    named = {0: NamedBarrier(nw + NH), 1: NamedBarrier(NH), 2: NamedBarrier(nw)}
+    res = [Barrier(nh), Barrier(nh)]
+    fold = Barrier(nh)
+    tfold = [Barrier(nh) for _ in range(nw)]
+    named = {0: NamedBarrier(nw + nh), 1: NamedBarrier(nh), 2: NamedBarrier(nw)}
     events = []        # (time, action) of the asynchronous engines
     last_mma = {}      # per warp: completion time of its latest MMA group
     now = [0]
@@ -136,7 +140,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
         def land():
             inflight['copy'] -= 1
             landed.add(g)
-            for _ in range(NH):
+            for _ in range(nh):
                 staged[b].arrive()
 
         def land_bx():
@@ -160,6 +164,18 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                 for gi in range(ngr):
                     gr = gg + ch * ngr + gi
                     sl = gs + ch * ksc + gi * fk + fk - 1       # the group's last k-step
+                    if tile_fold:
+                        for w in range(nw):
+                            if fold_wait == 'chunk':
+                                yield from wait(chunk[w], gr & 1)
+                            else:
+                                yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+                            check((w, gr) in mma_done, 'fold of group %d before its MMAs completed' % gr)
+                            check((w, gr + 1) not in mma_issued, 'fold of group %d while group %d runs' % (gr, gr + 1))
+                            folded.setdefault((w, gr), set()).add(h)
+                            yield
+                            tfold[w].arrive()
+                        continue
                     for w in range(nw):
                         if fold_wait == 'chunk':
                             yield from wait(chunk[w], gr & 1)
@@ -214,7 +230,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                 if g >= 2:
                     yield from wait(res[b], ((g >> 1) & 1) ^ 1)
                 check(g in landed, 'law of chunk %d before its tables' % g)
-                check(g < 2 or len(res_done.get(g - 2, ())) == NH, 'w P of chunk %d overwritten' % (g - 2))
+                check(g < 2 or len(res_done.get(g - 2, ())) == nh, 'w P of chunk %d overwritten' % (g - 2))
                 readers[g] = readers.get(g, 0) + 1
                 wp_written.setdefault(g, set()).add(w)
                 wp[b].arrive()
@@ -235,8 +251,9 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                     if ks == (1 if defer else 0):
                         yield from wait(bx[b], (g >> 1) & 1)
                     if first and gr >= 1:
-                        yield from wait(fold, (gr - 1) & 1)
-                        check(len(folded.get((w, gr - 1), ())) == NH, 'MMAs of group %d before the fold' % gr)
+                        fb = fold if not tile_fold else tfold[w if tile_fold == 'own' else 0]
+                        yield from wait(fb, (gr - 1) & 1)
+                        check(len(folded.get((w, gr - 1), ())) == nh, 'MMAs of group %d before the fold' % gr)
                     if err[0]:                   # no MMA is issued after a timeout
                         pending.discard((w, s))
                         pending.discard((w, s - 1))
@@ -270,7 +287,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
             yield from drain_wait(lambda: inflight['mma'][w] == 0)
         yield from sync(0)
 
-    agents = [helper(h) for h in range(NH)] + [tile(w) for w in range(nw)]
+    agents = [helper(h) for h in range(nh)] + [tile(w) for w in range(nw)]
     alive = list(range(len(agents)))
     steps = 0
     while alive:
@@ -297,21 +314,24 @@ def test_protocol_is_hazard_free(seed):
 
 
 @pytest.mark.parametrize('seed', range(40))
-@pytest.mark.parametrize('nw,ksc,fk', [(3, 8, 2), (5, 4, 2), (5, 4, 4)])
-def test_wide_kernel_protocol_is_hazard_free(seed, nw, ksc, fk):
+@pytest.mark.parametrize('nw,ksc,fk,nh', [(3, 8, 2, 8), (3, 8, 2, 4), (5, 4, 2, 4), (5, 4, 4, 4)])
+def test_wide_kernel_protocol_is_hazard_free(seed, nw, ksc, fk, nh):
     # the wide kernel: fewer tile warps, fold groups of fk k-steps within a
-    # chunk (chunk and fold barriers advance once per group)
-    assert not run_schedule(seed, n_tiles=seed % 4, nch=1 + (seed // 3) % 5, nw=nw, ksc=ksc, fk=fk, defer=True)
+    # chunk (chunk and fold barriers advance once per group), a fold barrier
+    # per tile, 4 or 8 helper warps
+    assert not run_schedule(seed, n_tiles=seed % 4, nch=1 + (seed // 3) % 5, nw=nw, ksc=ksc, fk=fk, defer=True,
+                            nh=nh, tile_fold='own')
 
 
 @pytest.mark.parametrize('seed', range(20))
 def test_wide_kernel_timeouts_end_after_a_drain(seed):
     nt, nch = 1 + seed % 3, 1 + (seed // 3) % 5
     latency = 30 if seed % 2 else 400
-    span = run_schedule(seed, nt, nch, latency=latency, clock=True, nw=3, ksc=8, fk=2, defer=True)
+    kw = dict(nw=3, ksc=8, fk=2, defer=True, nh=8, tile_fold='own')
+    span = run_schedule(seed, nt, nch, latency=latency, clock=True, **kw)
     r = random.Random(seed)
     at = r.randrange(span) if seed % 3 else max(0, span - r.randrange(1, latency))
-    run_schedule(seed, nt, nch, latency=latency, timeout_at=at, nw=3, ksc=8, fk=2, defer=True)
+    run_schedule(seed, nt, nch, latency=latency, timeout_at=at, **kw)
 
 
 def test_wide_kernel_wrong_fold_wait_is_caught():
@@ -322,7 +342,8 @@ def test_wide_kernel_wrong_fold_wait_is_caught():
     hits = 0
     for seed in range(6):
         try:
-            run_schedule(seed, n_tiles=2, nch=3, fold_wait='buffer', max_steps=60_000, nw=5, ksc=4, fk=4, defer=True)
+            run_schedule(seed, n_tiles=2, nch=3, fold_wait='buffer', max_steps=60_000, nw=5, ksc=4, fk=4, defer=True,
+                         tile_fold='own')
         except Hazard as e:
             assert 'before its MMAs completed' in str(e)
             hits += 1
@@ -505,5 +526,19 @@ def test_single_role_buffer_wait_is_caught():
             run_single_role(seed, n_tiles=1, nch=4, fold_wait='buffer')
         except Hazard as e:
             assert 'before its MMAs completed' in str(e)
+            hits += 1
+    assert hits > 0
+
+
+def test_wide_kernel_wrong_tile_fold_wait_is_caught():
+    # every tile warp waiting on tile 0's fold barrier instead of its own
+    # issues MMAs onto accumulators the helpers have not folded yet
+    hits = 0
+    for seed in range(8):
+        try:
+            run_schedule(seed, n_tiles=2, nch=3, max_steps=60_000, nw=3, ksc=8, fk=2, defer=True, nh=8,
+                         tile_fold='first')
+        except Hazard as e:
+            assert 'before the fold' in str(e) or 'while group' in str(e)
             hits += 1
     assert hits > 0
