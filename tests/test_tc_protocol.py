@@ -72,7 +72,8 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
     wide kernel).  nh helper warps.  tile_fold: one fold barrier per tile,
     arrived at as each tile is folded ('own': each tile warp waits on its
     tile's barrier, the wide kernel; 'first': every tile warp waits on tile
-    0's barrier, a wrong wait); None: one fold barrier after all tiles."""
+    0's barrier, a wrong wait); None: one fold barrier after all tiles (the
+    warp-specialized kernel)."""
     fk = ksc if fk is None else fk
     ngr = ksc // fk
     rng = random.Random(seed)
@@ -150,6 +151,16 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
         later(land)
         later(land_bx)
 
+    def group_wait(w, gr, sl):
+        # the fold's wait for the MMAs of group gr (last k-step sl) of warp w
+        if fold_wait == 'chunk':
+            yield from wait(chunk[w], gr & 1)
+        elif fold_wait == 'buffer':
+            yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+        else:  # both phases of the buffer barrier in turn
+            yield from wait(commit[w][sl & 1], ((sl >> 1) & 1) ^ 1)
+            yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+
     def helper(h):
         gc = gs = gg = 0
         for _ in range(n_tiles):
@@ -166,10 +177,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                     sl = gs + ch * ksc + gi * fk + fk - 1       # the group's last k-step
                     if tile_fold:
                         for w in range(nw):
-                            if fold_wait == 'chunk':
-                                yield from wait(chunk[w], gr & 1)
-                            else:
-                                yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+                            yield from group_wait(w, gr, sl)
                             check((w, gr) in mma_done, 'fold of group %d before its MMAs completed' % gr)
                             check((w, gr + 1) not in mma_issued, 'fold of group %d while group %d runs' % (gr, gr + 1))
                             folded.setdefault((w, gr), set()).add(h)
@@ -177,13 +185,7 @@ def run_schedule(seed, n_tiles, nch, fold_wait='chunk', max_steps=400_000, timeo
                             tfold[w].arrive()
                         continue
                     for w in range(nw):
-                        if fold_wait == 'chunk':
-                            yield from wait(chunk[w], gr & 1)
-                        elif fold_wait == 'buffer':
-                            yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
-                        else:  # both phases of the buffer barrier in turn
-                            yield from wait(commit[w][sl & 1], ((sl >> 1) & 1) ^ 1)
-                            yield from wait(commit[w][sl & 1], (sl >> 1) & 1)
+                        yield from group_wait(w, gr, sl)
                     for w in range(nw):
                         check((w, gr) in mma_done, 'fold of group %d before its MMAs completed' % gr)
                         check((w, gr + 1) not in mma_issued, 'fold of group %d while group %d runs' % (gr, gr + 1))
