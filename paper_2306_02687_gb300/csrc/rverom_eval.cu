@@ -94,7 +94,7 @@ int forward_candidates(int dim, int n, bool mixed, LaunchFn *out, int max_out, C
         } else if (n <= 64) {
             add(RV_SYM(2, 72, 6, 3, 16, float), "simt-symmetric <2,72> 6x6 blocks, 3 points x 16 ECM", 1);
             add(RV_FUSED(2, 72, 9, 9, 4, 8, float), "simt-fused <2,72> 4 points x 8 ECM", 1);
-            add(RV_TCW(2, 68, 16, 2), "tcgen05-tf32x3 wide <2,68> 3 tile + 4 helper warps, 6 points x 16 ECM, fold per 2 k-steps", 2);
+            add(RV_TCW(2, 68, 16, 2), "tcgen05-tf32x3 wide <2,68> 3 tile + 8 helper warps, 6 points x 16 ECM, fold per 2 k-steps", 2);
         }
     } else if (dim == 2) {
         if (n <= 12) add(RV_FUSED(2, 16, 4, 4, 16, 8, double), "fp64-fused <2,16> 16 points x 8 ECM", 1);
