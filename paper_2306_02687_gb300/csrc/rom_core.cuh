@@ -170,6 +170,37 @@ __device__ __forceinline__ void nh_tangent_row(const KT *fi, KT lam, KT c3, KT m
         }
 }
 
+// The same row for an index c known only at run time (one row per lane):
+// the entries of F^-1 that depend on i or J are picked by selects, so that
+// fi stays in registers and only the lane's own row is formed.
+template <int D, typename KT>
+__device__ __forceinline__ void nh_tangent_row_rt(const KT *fi, KT lam, KT c3, KT mu, int c, KT *Arow) {
+    const int i = c / D, J = c % D;
+    KT fLi[D], fJk[D];  // Fi_Li and Fi_Jk for L, k = 0 .. D-1
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        fLi[t] = fi[t * D];
+        fJk[t] = fi[t];
+#pragma unroll
+        for (int u = 1; u < D; ++u) {
+            if (i == u) fLi[t] = fi[t * D + u];
+            if (J == u) fJk[t] = fi[u * D + t];
+        }
+    }
+    KT fJi = fJk[0];  // Fi_Ji
+#pragma unroll
+    for (int u = 1; u < D; ++u)
+        if (i == u) fJi = fJk[u];
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int L = 0; L < D; ++L) {
+            KT v = lam * fJi * fi[L * D + k] + c3 * fLi[L] * fJk[k];
+            if (i == k && J == L) v += mu;
+            Arow[k * D + L] = v;
+        }
+}
+
 // Neo-Hooke stress in double-float: P = mu F + ((lam lnJ - mu)/J) cof(F),
 // F^-T = cof(F)/J.  Also returns F^-1 and ln J in float32 for the tangent.
 template <int D>
@@ -1334,15 +1365,7 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
                             s_WPl[(il * G + c) * NP + p] = wp.lo;
                             const KT muk = ph ? kmu1 : kmu0, lam = ph ? klam1 : klam0;
                             const KT c3 = muk - lam * (KT)lnf;
-#pragma unroll
-                            for (int r = 0; r < G; ++r) {  // row c of the tangent (compile-time indices)
-                                KT Ar2[G];
-                                nh_tangent_row<D, KT>(fi, lam, c3, muk, r, Ar2);
-                                if (r == c) {
-#pragma unroll
-                                    for (int c2 = 0; c2 < G; ++c2) Ar[c2] = Ar2[c2];
-                                }
-                            }
+                            nh_tangent_row_rt<D, KT>(fi, lam, c3, muk, c, Ar);  // row c of the tangent
                             const KT *Bx = s_Bx + il * G * NA;
                             const KT wk = (KT)s_wh[il];
                             for (int b = 0; b < n; ++b) {
