@@ -240,6 +240,55 @@ __device__ __forceinline__ bool nh_stress_df(const df *F, df mu, df lam, df *P, 
     return true;
 }
 
+// The law of nh_stress_df spread over a group of LPT lanes, lane c < G
+// holding F_c: lane c forms cofactor c and stress entry P_c only; F, J and
+// the cofactors reach the lanes that need them by shuffles, and every lane
+// gets ln J and F^-1 (float32).  Per entry the operations and their order
+// are those of nh_stress_df.  Every lane of the warp calls it (it shuffles),
+// so a failed J does not return early: the result is then discarded.
+template <int D, int LPT>
+__device__ __forceinline__ bool nh_stress_df_split(df Fc, int c, df mu, df lam, df &Pc, float *fi, float &lnJf) {
+    constexpr int G = D * D;
+    static_assert(G <= LPT, "one lane per entry");
+    const int cc = c < G ? c : 0;
+    auto sh = [](df v, int src) {
+        return df{__shfl_sync(0xffffffffu, v.hi, src, LPT), __shfl_sync(0xffffffffu, v.lo, src, LPT)};
+    };
+    df cof, J;
+    if constexpr (D == 2) {
+        const df o = sh(Fc, 3 - cc);  // cof = [F3, -F2, -F1, F0]
+        cof = (cc == 0 || cc == 3) ? o : df_neg(o);
+        J = df_sub(df_mul(sh(Fc, 0), sh(Fc, 3)), df_mul(sh(Fc, 1), sh(Fc, 2)));
+    } else {
+        // cofactor (i, j) from rows r1 < r2 != i, columns j + 1, j + 2 (mod 3),
+        // swapped for the middle row so that the sign is in the product order
+        const int i = cc / 3, j = cc % 3;
+        const int r1 = i == 0 ? 1 : 0, r2 = i == 2 ? 1 : 2;
+        int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        if (i == 1) {
+            const int t = j1;
+            j1 = j2;
+            j2 = t;
+        }
+        const df fa = sh(Fc, r1 * 3 + j1), fb = sh(Fc, r2 * 3 + j2);
+        const df fd = sh(Fc, r1 * 3 + j2), fe = sh(Fc, r2 * 3 + j1);
+        cof = df_sub(df_mul(fa, fb), df_mul(fd, fe));
+        J = df_add(df_add(df_mul(sh(Fc, 0), sh(cof, 0)), df_mul(sh(Fc, 1), sh(cof, 1))), df_mul(sh(Fc, 2), sh(cof, 2)));
+    }
+    const bool ok = J.hi > 0.0f && isfinite(J.hi);
+    const df Js = ok ? J : df{1.0f, 0.0f};
+    const df lnJ = df_log(Js);
+    const df rJ = df_div(df{1.0f, 0.0f}, Js);
+    const df coef = df_mul(df_sub(df_mul(lam, lnJ), mu), rJ);
+    Pc = df_add(df_mul(mu, Fc), df_mul(coef, cof));
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int q = 0; q < D; ++q) fi[r * D + q] = __fmul_rn(__shfl_sync(0xffffffffu, cof.hi, q * D + r, LPT), rJ.hi);
+    lnJf = lnJ.hi;
+    return ok;
+}
+
 // ---------------------------------------------------------------------------
 // polar decomposition F = R U.  2D: closed form; 3D: Newton iteration
 // X <- (X + X^-T)/2 on the rotation (quadratically convergent, bounded).
@@ -1338,28 +1387,19 @@ __global__ void __launch_bounds__(Plan<D, NA, TA, TB, NP, CI, KT, SYM>::NT)
                         for (; j < n; ++j) dacc_fma(s4[0], Bh[j], Bl[j], qh[j], ql[j]);
                         Fc = df_add(df_add(dacc_get(s4[0]), dacc_get(s4[1])), df_add(dacc_get(s4[2]), dacc_get(s4[3])));
                     }
-                    df F[G];
-#pragma unroll
-                    for (int c2 = 0; c2 < G; ++c2) {
-                        F[c2].hi = __shfl_sync(0xffffffffu, Fc.hi, c2, LPT);
-                        F[c2].lo = __shfl_sync(0xffffffffu, Fc.lo, c2, LPT);
-                    }
-                    df P[G];
+                    df Pc;
                     float fif[G], lnf = 0.0f;
-                    if (live && !nh_stress_df<D>(F, ph ? dmu1 : dmu0, ph ? dlam1 : dlam0, P, fif, lnf)) {
+                    const bool lok = nh_stress_df_split<D, LPT>(Fc, c, ph ? dmu1 : dmu0, ph ? dlam1 : dlam0, Pc, fif, lnf);
+                    if (live && !lok) {
                         if (c == 0) atomicCAS(&s_flag[p], ST_OK, ST_DETF);
-                        live = false;  // the same F in every lane of the group: the same decision
+                        live = false;  // the same J in every lane of the group: the same decision
                     }
                     if (valid && c < G) {
                         KT *yr = s_Y + ((il * G + c) * NP + p) * NAP;  // row k = il*G + c
                         if (live) {
-                            df Pc = P[0];
                             KT fi[G], Ar[G];
 #pragma unroll
-                            for (int c2 = 0; c2 < G; ++c2) {
-                                if (c2 == c) Pc = P[c2];
-                                fi[c2] = (KT)fif[c2];
-                            }
+                            for (int c2 = 0; c2 < G; ++c2) fi[c2] = (KT)fif[c2];
                             const df wp = df_mul(df{s_wh[il], s_wl[il]}, Pc);
                             s_WPh[(il * G + c) * NP + p] = wp.hi;
                             s_WPl[(il * G + c) * NP + p] = wp.lo;
