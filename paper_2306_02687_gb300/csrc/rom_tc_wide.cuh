@@ -66,7 +66,7 @@ struct TcWidePlan {
     static constexpr int RPH = (NP * NQ + NHT - 1) / NHT;  // residual rows per helper thread
     static constexpr int TCOLS = 2 * NW * NN;       // accumulator + running sum
     static constexpr int TALLOC = TCOLS <= 256 ? 256 : 512;
-    static constexpr int SOFF = TALLOC / 2;         // running sums: a 32-column-aligned offset
+    static constexpr int SOFF = TALLOC / 2;         // first column of the running sums
     static constexpr int NKF = G * (G + 1) / 2;     // K_FF entries (symmetric)
     static_assert(D == 2, "planar RVEs (two ECM points per k-step)");
     static_assert(NAR == 32 || NAR == 64, "32 or 64 mode rows per point");
@@ -76,7 +76,7 @@ struct TcWidePlan {
     static_assert(NN % 16 == 0 && NW >= 1, "fold in blocks of 16 columns");
     static_assert(NP * G <= NHT, "one homogenized-stress entry per helper thread");
     static_assert(TCOLS <= 512, "TMEM holds 512 columns");
-    static_assert(NW * NN <= SOFF && SOFF % 32 == 0, "accumulators, then running sums from column SOFF");
+    static_assert(NW * NN <= SOFF, "accumulators, then running sums from column SOFF");
     // byte offsets
     static constexpr size_t YWARP = 4 * 4096;  // per tile warp: [2 buffers][hi|lo][2 kg][16 rg][8][4] floats
     static constexpr size_t o_Y = 0;
